@@ -1,0 +1,157 @@
+"""Seeded synthetic snapshot matrices (inputs only, no POD arithmetic).
+
+Both the CUDA path and the FP64 oracle consume the arrays made here; this
+module holds none of the method's steps.  The paper's datasets (Faces, the
+V_2D CFD velocities, the cropped and full Yale faces; Sec. 1) are not
+available, so these stand in for them with the same shape class (tall, thin,
+row-mean-centred snapshot matrices) and a spectrum that is known by
+construction.
+
+All randomness comes from ``numpy.random.default_rng(seed)`` (PCG64).  Every
+matrix is column-major in the sense of the library: column j is snapshot j.
+The arrays returned are C-contiguous (n, m) buffers viewed as (m, n) with
+``.T``, i.e. Fortran order, so each snapshot is contiguous in memory.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+
+def haar(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    """Haar-distributed orthonormal columns: Q of a Gaussian matrix with the
+    sign of diag(R) made positive (Mezzadri 2007)."""
+    G = rng.standard_normal((rows, cols))
+    Q, R = np.linalg.qr(G, mode="reduced")
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d
+
+
+def _finish(A64_t: np.ndarray, dtype, center: bool) -> np.ndarray:
+    """A64_t is (n, m) FP64 (row j = snapshot j).  Mean-centre the rows of A
+    (i.e. subtract, for every spatial index, its mean over snapshots), round
+    to the storage dtype, return the (m, n) Fortran-ordered view."""
+    if center:
+        A64_t -= A64_t.mean(axis=0, keepdims=True)
+    out = np.ascontiguousarray(A64_t, dtype=dtype)
+    return out.T
+
+
+def planted(m: int, n: int, sigma, noise: float, seed: int, dtype=np.float64,
+            center: bool = True) -> np.ndarray:
+    """A = U diag(sigma) V^T + noise * N(0, 1), U and V Haar, rows centred."""
+    rng = np.random.default_rng(seed)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    rho = sigma.size
+    U = haar(rng, m, rho)
+    V = haar(rng, n, rho)
+    At = (V * sigma) @ U.T                      # (n, m)
+    if noise > 0:
+        At += noise * rng.standard_normal((n, m))
+    return _finish(At, dtype, center)
+
+
+def planted_factors(m: int, n: int, sigma, seed: int):
+    """The exact factors of ``planted(..., noise=0, center=False)``."""
+    rng = np.random.default_rng(seed)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    U = haar(rng, m, sigma.size)
+    V = haar(rng, n, sigma.size)
+    return U, sigma, V
+
+
+@dataclass
+class FlowModes:
+    a: np.ndarray       # x wavenumbers
+    b: np.ndarray       # y wavenumbers
+    omega: np.ndarray   # temporal frequencies
+    amp: np.ndarray     # amplitudes
+
+
+def flow_modes(modes: int, seed: int, max_k: int = 40, max_omega: int = 200) -> FlowModes:
+    rng = np.random.default_rng(seed)
+    pairs = rng.choice(max_k * max_k, size=modes, replace=False)
+    a = pairs // max_k + 1
+    b = pairs % max_k + 1
+    omega = rng.choice(max_omega, size=modes, replace=False) + 1
+    amp = np.arange(1, modes + 1, dtype=np.float64) ** -1.5
+    return FlowModes(a=a, b=b, omega=omega, amp=amp)
+
+
+def flow(grid: int, n: int, modes: int, noise: float, seed: int, dtype=np.float32,
+         center: bool = True, max_k: int = 40, max_omega: int = 200) -> np.ndarray:
+    """Flow-like snapshots on a grid x grid periodic mesh:
+    A[(p, q), s] = sum_j amp_j sin(a_j x_p + omega_j t_s) cos(b_j y_q) + noise,
+    x_p = 2 pi p / grid, y_q = 2 pi q / grid, t_s = 2 pi s / n, row index
+    p * grid + q.  Distinct integer wavenumbers below grid/2 and distinct
+    integer frequencies below n/2 make every term orthogonal on the mesh, so
+    the noiseless spectrum is amp_j * sqrt(m n / 8), each value twice."""
+    fm = flow_modes(modes, seed, max_k, max_omega)
+    rng = np.random.default_rng(seed + 1)
+    x = 2 * np.pi * np.arange(grid) / grid
+    ts = 2 * np.pi * np.arange(n) / n
+    # sin(a x + w t) cos(b y) = sin(a x) cos(b y) cos(w t) + cos(a x) cos(b y) sin(w t)
+    sx = np.sin(np.outer(x, fm.a))              # (grid, modes)
+    cx = np.cos(np.outer(x, fm.a))
+    cy = np.cos(np.outer(x, fm.b))
+    Fs = (sx[:, None, :] * cy[None, :, :]).reshape(grid * grid, modes)
+    Fc = (cx[:, None, :] * cy[None, :, :]).reshape(grid * grid, modes)
+    Gc = np.cos(np.outer(ts, fm.omega)) * fm.amp
+    Gs = np.sin(np.outer(ts, fm.omega)) * fm.amp
+    At = Gc @ Fs.T + Gs @ Fc.T                  # (n, m)
+    if noise > 0:
+        At += noise * rng.standard_normal(At.shape)
+    return _finish(At, dtype, center)
+
+
+def flow_spectrum(grid: int, n: int, modes: int, seed: int, max_k: int = 40,
+                  max_omega: int = 200) -> np.ndarray:
+    """Closed-form singular values of the noiseless ``flow`` matrix, sorted."""
+    fm = flow_modes(modes, seed, max_k, max_omega)
+    m = grid * grid
+    s = np.repeat(fm.amp * np.sqrt(m * n / 8.0), 2)
+    return np.sort(s)[::-1]
+
+
+# ----------------------------------------------------------------------------
+# The workloads used by the tests and the benchmark
+# ----------------------------------------------------------------------------
+SEED_DATA = 0x19050510
+SEED_SAMPLING = 0x5107
+
+
+@dataclass
+class Workload:
+    name: str
+    m: int
+    n: int
+    k: int
+    c: int
+    dtype: type
+    tol: float
+    description: str
+
+
+PLANTED_SMALL = Workload(
+    "planted-2000x500-f64", 2000, 500, 10, 20, np.float64, 1e-8,
+    "planted sigma_i = 10^(-i/8), i < 40, Haar U (2000x40) and V (500x40), "
+    "N(0, 1e-6^2) noise, rows centred, FP64; k=10, c=20")
+
+FLOW_316 = Workload(
+    "flow-316x316x2000-f32", 316 * 316, 2000, 20, 40, np.float32, 1e-8,
+    "60 separable sin(a x + w t) cos(b y) modes on a 316x316 grid, 2000 "
+    "snapshots, amplitudes j^-1.5, N(0, 1e-3^2) noise, rows centred, FP32; "
+    "k=20, c=40")
+
+
+def make_planted_small(seed: int = SEED_DATA + 1, dtype=np.float64) -> np.ndarray:
+    sigma = 10.0 ** (-np.arange(40) / 8.0)
+    return planted(2000, 500, sigma, 1e-6, seed, dtype)
+
+
+def make_flow_316(seed: int = SEED_DATA + 2, dtype=np.float32, grid: int = 316,
+                  n: int = 2000) -> np.ndarray:
+    return flow(grid, n, 60, 1e-3, seed, dtype)
