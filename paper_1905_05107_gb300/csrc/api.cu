@@ -1,0 +1,883 @@
+// C ABI of the library (include/pod.h): context life cycle, the ISMA
+// iteration driver (Algorithm 1), the closing refinement and the step-level
+// entry points.  One round of Algorithm 1 is a fixed sequence of kernels
+// whose sizes live in device memory (DevState); it is captured once into a
+// CUDA graph and replayed, and the host reads the 80-byte state only between
+// batches of rounds.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "pod_internal.h"
+
+
+
+namespace {
+
+template <typename T>
+__global__ void k_write_modes(const T *U, int64_t m, int r_cur, int k, const double *sigma,
+                              const double *dots, T *U_out, double *sigma_out) {
+    const int64_t total = m * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e / m);
+        const int64_t i = e - (int64_t)l * m;
+        T v = (T)0;
+        if (l < r_cur) v = dots[l] < 0.0 ? -U[(int64_t)l * m + i] : U[(int64_t)l * m + i];
+        U_out[(int64_t)l * m + i] = v;
+    }
+    if (blockIdx.x == 0)
+        for (int l = threadIdx.x; l < k; l += blockDim.x) sigma_out[l] = l < r_cur ? sigma[l] : 0.0;
+}
+
+// V_out[:, l] = sign_l * (Y K)[:, l]; Y column-major n x r (ld n), K r x r (ld r)
+template <typename T>
+__global__ void k_write_v(const double *Y, const double *K, int64_t n, int r, int k, const double *dots,
+                          T *V_out) {
+    const int64_t total = n * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e / n);
+        const int64_t j = e - (int64_t)l * n;
+        double v = 0.0;
+        if (l < r) {
+            for (int q = 0; q < r; ++q) v += Y[(int64_t)q * n + j] * K[q * r + l];
+            if (dots[l] < 0.0) v = -v;
+        }
+        V_out[(int64_t)l * n + j] = (T)v;
+    }
+}
+
+__global__ void k_set_state(DevState *st, int r_cur, int g, int r_new, int t, int remaining) {
+    if (threadIdx.x == 0) {
+        DevState s{};
+        s.t = t;
+        s.r_cur = r_cur;
+        s.g = g;
+        s.r_new = r_new;
+        s.remaining = remaining;
+        *st = s;
+    }
+}
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return sms > 0 ? sms : 148;
+}
+
+template <typename V>
+pod_status dalloc(V **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc((void **)p, count * sizeof(V)) != cudaSuccess) {
+        cudaGetLastError();
+        return POD_ENOMEM;
+    }
+    return POD_OK;
+}
+
+}  // namespace
+
+struct pod_ctx {
+    pod_params p;
+    const void *A;
+    cudaStream_t stream;
+    int rmax, cmax, nmax;
+    int rtrunc;         // truncation rank of a merge (<= rmax)
+    int core_f64;
+    int sms;
+    TallPlan plan;
+    AtuPlan aplan;
+    // device buffers
+    void *U;
+    double *sigma, *s, *ort, *Y;
+    uint8_t *mask, *flags;
+    uint64_t *w, *cdf;
+    int32_t *draws, *idx, *hist_idx, *hist_g;
+    double *hist_measure;
+    DevState *st, *aux;
+    double *part, *part_atu;
+    double *P, *PG, *G2, *Ptot, *M1, *R1p, *E, *Xm, *Ym;
+    double *rG, *rG2, *rM1, *rR1p, *rsig, *rVR, *rK, *dots, *part_sign;
+    int32_t *replay_idx, *replay_off;
+    int replay_T;
+    // host
+    DevState *hstate;   // pinned mirror
+    cudaGraphExec_t graph;
+    bool graph_ready, graph_failed;
+    bool poisoned;
+    bool refined;
+    int refined_r;
+    int sign_grid;
+    // kernel launches issued (host count) and per-launch event marks
+    long long launches;
+    int graph_kernels;
+    cudaEvent_t *prof_ev;
+    int prof_n, prof_cap;
+};
+
+static void mark(pod_ctx *c) {
+    c->launches += 1;
+    if (c->prof_ev && c->prof_n < c->prof_cap) cudaEventRecord(c->prof_ev[c->prof_n++], c->stream);
+}
+
+static void ctx_free(pod_ctx *c) {
+    if (!c) return;
+    if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+    void *bufs[] = {c->U, c->sigma, c->s, c->ort, c->Y, c->mask, c->flags, c->w, c->cdf, c->draws,
+                    c->idx, c->hist_idx, c->hist_g, c->hist_measure, c->st, c->aux, c->part,
+                    c->part_atu, c->P, c->PG, c->G2, c->Ptot, c->M1, c->R1p, c->E, c->Xm, c->Ym,
+                    c->rG, c->rG2, c->rM1, c->rR1p, c->rsig, c->rVR, c->rK, c->dots, c->part_sign,
+                    c->replay_idx, c->replay_off};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (c->hstate) cudaFreeHost(c->hstate);
+    free(c);
+}
+
+static pod_status check_params(const pod_params *p) {
+    if (!p) return POD_EINVAL;
+    if (p->m <= 0 || p->n <= 0 || p->lda < p->m) return POD_EINVAL;
+    if (p->n > 0x7fffffffLL) return POD_EINVAL;
+    if (p->k < 1 || p->k > p->m || p->k > p->n) return POD_EINVAL;
+    if (p->c < 1) return POD_EINVAL;
+    const int r = p->r > 0 ? p->r : p->k;
+    if (r < p->k) return POD_EINVAL;
+    if (p->dtype != POD_F32 && p->dtype != POD_F64) return POD_EINVAL;
+    if (p->col_strategy < POD_L2N || p->col_strategy > POD_ORT) return POD_EINVAL;
+    if (p->criterion != POD_SUBSPACE && p->criterion != POD_MODES) return POD_EINVAL;
+    if (p->core < POD_CORE_AUTO || p->core > POD_CORE_F64) return POD_EINVAL;
+    if (p->rows != 0) return POD_EUNSUPPORTED;
+    if (!(p->tol == p->tol)) return POD_EINVAL;
+    return POD_OK;
+}
+
+template <typename T>
+static TallArgs<T> tall_args(pod_ctx *c, double *part, int64_t stride) {
+    TallArgs<T> a{};
+    a.m = c->p.m;
+    a.A = (const T *)c->A;
+    a.lda = c->p.lda;
+    a.idx = c->idx;
+    a.U = (T *)c->U;
+    a.ldu = c->p.m;
+    a.st = c->st;
+    a.rmax = c->rmax;
+    a.cmax = c->cmax;
+    a.bm = c->plan.bm;
+    a.part = part;
+    a.part_stride = stride;
+    a.P = c->P;
+    a.P2 = c->PG;
+    a.M1 = c->M1;
+    a.Xm = c->Xm;
+    a.Ym = c->Ym;
+    return a;
+}
+
+static SmallArgs small_args(pod_ctx *c) {
+    SmallArgs s{};
+    s.st = c->st;
+    s.dtype = c->p.dtype;
+    s.core_f64 = c->core_f64;
+    s.m = c->p.m;
+    s.k = c->p.k;
+    s.r = c->rtrunc;
+    s.c = c->p.c;
+    s.rmax = c->rmax;
+    s.cmax = c->cmax;
+    s.criterion = c->p.criterion;
+    s.tol = c->p.tol;
+    s.max_iter = c->p.max_iter;
+    s.sigma = c->sigma;
+    s.P = c->P;
+    s.PG = c->PG;
+    s.G2 = c->G2;
+    s.Ptot = c->Ptot;
+    s.M1 = c->M1;
+    s.R1p = c->R1p;
+    s.E = c->E;
+    s.Xm = c->Xm;
+    s.Ym = c->Ym;
+    s.hist_measure = c->hist_measure;
+    return s;
+}
+
+// One round of Algorithm 1 (probabilities, draws, GET UPDATE, BLOCK MERGE,
+// convergence test) as a fixed launch sequence.
+template <typename T>
+static pod_status enqueue_round(pod_ctx *c) {
+    cudaStream_t s = c->stream;
+    const int64_t sPG = (int64_t)c->rmax * c->cmax + (int64_t)c->cmax * c->cmax;
+    if (c->p.col_strategy == POD_ORT) {
+        AtuArgs<T> aa{};
+        aa.m = c->p.m;
+        aa.n = c->p.n;
+        aa.A = (const T *)c->A;
+        aa.lda = c->p.lda;
+        aa.U = (const T *)c->U;
+        aa.ldu = c->p.m;
+        aa.st = c->st;
+        aa.mask = c->mask;
+        aa.ldy = (int)c->p.n;
+        aa.rmax = c->rmax;
+        aa.part = c->part_atu;
+        POD_TRY(launch_atu<T>(aa, c->aplan, s));
+        mark(c);
+        POD_TRY(launch_reduce(c->part_atu, c->aplan.split, (int64_t)c->p.n * c->rmax,
+                              (int64_t)c->p.n * c->rmax, c->Y, c->st, s));
+        mark(c);
+        POD_TRY(launch_ort_values(c->s, c->Y, c->p.n, (int)c->p.n, c->st, c->mask, c->ort, s));
+        mark(c);
+    }
+    SampleArgs sa{};
+    sa.n = c->p.n;
+    sa.c = c->p.c;
+    sa.L = weight_bits(c->p.n);
+    sa.mode_round0 = 0;
+    sa.mode = c->p.col_strategy == POD_L2N ? 0 : (c->p.col_strategy == POD_UNF ? 1 : 2);
+    sa.seed = c->p.seed;
+    sa.stream_id = 0;
+    sa.s = c->s;
+    sa.ort = c->ort;
+    sa.w = c->w;
+    sa.cdf = c->cdf;
+    sa.mask = c->mask;
+    sa.flags = c->flags;
+    sa.draws = c->draws;
+    sa.idx = c->idx;
+    sa.st = c->st;
+    sa.replay_idx = c->replay_idx;
+    sa.replay_off = c->replay_off;
+    sa.replay_T = c->replay_T;
+    sa.hist_idx = c->hist_idx;
+    sa.hist_g = c->hist_g;
+    POD_TRY(launch_sample(sa, s));
+    mark(c);
+
+    TallArgs<T> ta = tall_args<T>(c, c->part, (int64_t)c->rmax * c->cmax);
+    POD_TRY(launch_tall<T>(TALL_PROJ, ta, c->plan, s));
+    mark(c);
+    POD_TRY(launch_reduce(c->part, c->plan.grid, ta.part_stride, ta.part_stride, c->P, c->st, s));
+    mark(c);
+    ta.part_stride = sPG;
+    ta.P = c->P;
+    POD_TRY(launch_tall<T>(TALL_CGS, ta, c->plan, s));
+    mark(c);
+    POD_TRY(launch_reduce(c->part, c->plan.grid, sPG, sPG, c->PG, c->st, s));
+    mark(c);
+    SmallArgs sm = small_args(c);
+    POD_TRY(launch_small_chol(sm, s));
+    mark(c);
+    ta.part_stride = (int64_t)c->cmax * c->cmax;
+    ta.P = c->P;
+    ta.P2 = c->PG;
+    ta.M1 = c->M1;
+    POD_TRY(launch_tall<T>(TALL_QR2, ta, c->plan, s));
+    mark(c);
+    POD_TRY(launch_reduce(c->part, c->plan.grid, ta.part_stride, ta.part_stride, c->G2, c->st, s));
+    mark(c);
+    POD_TRY(launch_core(sm, s));
+    mark(c);
+    POD_TRY(launch_tall<T>(TALL_UPDATE, ta, c->plan, s));
+    mark(c);
+    POD_TRY(launch_finish(c->st, s));
+    mark(c);
+    return POD_OK;
+}
+
+static pod_status enqueue_round_any(pod_ctx *c) {
+    return c->p.dtype == POD_F32 ? enqueue_round<float>(c) : enqueue_round<double>(c);
+}
+
+static pod_status build_graph(pod_ctx *c) {
+    if (c->graph_ready || c->graph_failed) return POD_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        c->graph_failed = true;
+        return POD_OK;
+    }
+    const long long before = c->launches;
+    pod_status st = enqueue_round_any(c);
+    c->graph_kernels = (int)(c->launches - before);
+    c->launches = before;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != POD_OK || e != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        c->graph_failed = true;
+        return st == POD_EUNSUPPORTED ? st : POD_OK;
+    }
+    if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        c->graph_failed = true;
+        return POD_OK;
+    }
+    cudaGraphDestroy(g);
+    c->graph_ready = true;
+    return POD_OK;
+}
+
+static pod_status read_state(pod_ctx *c) {
+    POD_CUDA_TRY(cudaMemcpyAsync(c->hstate, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    POD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return POD_OK;
+}
+
+template <typename T>
+static pod_status run_refine(pod_ctx *c) {
+    cudaStream_t s = c->stream;
+    const int r = c->hstate->r_cur;
+    const int64_t m = c->p.m, n = c->p.n;
+    if (r == 0) return POD_OK;
+    // Y = A^T U
+    k_set_state<<<1, 32, 0, s>>>(c->aux + 0, r, 0, 0, 1, 1);
+    c->launches += 1;
+    AtuArgs<T> aa{};
+    aa.m = m;
+    aa.n = n;
+    aa.A = (const T *)c->A;
+    aa.lda = c->p.lda;
+    aa.U = (const T *)c->U;
+    aa.ldu = m;
+    aa.st = c->aux + 0;
+    aa.mask = nullptr;
+    aa.ldy = (int)n;
+    aa.rmax = c->rmax;
+    aa.part = c->part_atu;
+    POD_TRY(launch_atu<T>(aa, c->aplan, s));
+    POD_TRY(launch_reduce(c->part_atu, c->aplan.split, n * c->rmax, n * r, c->Y, nullptr, s));
+    c->launches += 2;
+    // G = Y^T Y, CholeskyQR2 on the n x r matrix Y (FP64 tall passes)
+    TallPlan yplan = tall_plan(POD_F64, n, r, r, c->sms);
+    TallArgs<double> ya{};
+    ya.m = n;
+    ya.A = c->Y;
+    ya.lda = n;
+    ya.idx = nullptr;
+    ya.U = c->Y;
+    ya.ldu = n;
+    ya.rmax = r;
+    ya.cmax = r;
+    ya.bm = yplan.bm;
+    ya.part = c->part;
+    ya.part_stride = (int64_t)r * r;
+    if ((size_t)yplan.grid * r * r > (size_t)c->plan.grid * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax))
+        return POD_EUNSUPPORTED;
+    k_set_state<<<1, 32, 0, s>>>(c->aux + 1, r, r, 0, 1, 1);
+    c->launches += 1;
+    ya.st = c->aux + 1;
+    POD_TRY(launch_tall<double>(TALL_PROJ, ya, yplan, s));
+    POD_TRY(launch_reduce(c->part, yplan.grid, (int64_t)r * r, (int64_t)r * r, c->rG, nullptr, s));
+    c->launches += 2;
+    RefineArgs ra{};
+    ra.r = r;
+    ra.dtype = c->p.dtype;
+    ra.G = c->rG;
+    ra.G2 = c->rG2;
+    ra.M1 = c->rM1;
+    ra.R1p = c->rR1p;
+    ra.sigma = c->rsig;
+    ra.VR = c->rVR;
+    ra.K = c->rK;
+    POD_TRY(launch_refine_chol(ra, s));
+    c->launches += 1;
+    k_set_state<<<1, 32, 0, s>>>(c->aux + 2, 0, r, 0, 1, 1);
+    c->launches += 1;
+    ya.st = c->aux + 2;
+    ya.M1 = c->rM1;
+    POD_TRY(launch_tall<double>(TALL_QR2, ya, yplan, s));
+    POD_TRY(launch_reduce(c->part, yplan.grid, (int64_t)r * r, (int64_t)r * r, c->rG2, nullptr, s));
+    c->launches += 2;
+    POD_TRY(launch_refine_svd(ra, s));
+    c->launches += 1;
+    // U <- U V_R (in place)
+    k_set_state<<<1, 32, 0, s>>>(c->aux + 3, r, 0, r, 1, 1);
+    c->launches += 1;
+    TallArgs<T> ua = tall_args<T>(c, c->part, 0);
+    ua.st = c->aux + 3;
+    ua.rmax = r;
+    ua.cmax = c->cmax;
+    ua.Xm = c->rVR;
+    ua.Ym = c->Ym;
+    TallPlan uplan = tall_plan(c->p.dtype, m, r, c->cmax, c->sms);
+    ua.bm = uplan.bm;
+    POD_TRY(launch_tall<T>(TALL_UPDATE, ua, uplan, s));
+    c->launches += 1;
+    POD_CUDA_TRY(cudaMemcpyAsync(c->sigma, c->rsig, r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    c->refined = true;
+    c->refined_r = r;
+    return POD_OK;
+}
+
+template <typename T>
+static pod_status write_modes(pod_ctx *c, void *U_dev, double *sigma_dev, void *V_dev) {
+    cudaStream_t s = c->stream;
+    const int r = c->hstate->r_cur, k = c->p.k;
+    const int64_t m = c->p.m, n = c->p.n;
+    if (r > 0) {
+        POD_TRY(launch_sign_dots<T>((const T *)c->U, m, m, r, c->p.seed, c->part_sign, c->sign_grid, s));
+        POD_TRY(launch_reduce(c->part_sign, c->sign_grid, r, r, c->dots, nullptr, s));
+        c->launches += 2;
+    }
+    int grid = (int)((m * k + 255) / 256);
+    if (grid > 4 * c->sms) grid = 4 * c->sms;
+    if (grid < 1) grid = 1;
+    k_write_modes<T><<<grid, 256, 0, s>>>((const T *)c->U, m, r, k, c->sigma, c->dots, (T *)U_dev, sigma_dev);
+    POD_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    if (V_dev) {
+        int gv = (int)((n * k + 255) / 256);
+        if (gv > 4 * c->sms) gv = 4 * c->sms;
+        if (gv < 1) gv = 1;
+        k_write_v<T><<<gv, 256, 0, s>>>(c->Y, c->rK, n, c->refined ? c->refined_r : 0, k, c->dots, (T *)V_dev);
+        POD_CUDA_TRY(cudaGetLastError());
+        c->launches += 1;
+    }
+    return POD_OK;
+}
+
+extern "C" {
+
+const char *pod_strerror(pod_status s) {
+    switch (s) {
+        case POD_OK: return "ok";
+        case POD_EINVAL: return "invalid argument";
+        case POD_ENOMEM: return "out of memory";
+        case POD_ECUDA: return "CUDA runtime error";
+        case POD_ERANK: return "Cholesky breakdown";
+        case POD_ETIMEOUT: return "bounded device wait gave up";
+        case POD_ENAN: return "non-finite value in the core";
+        case POD_ESTATE: return "call not valid in the context's state";
+        case POD_EUNSUPPORTED: return "unsupported size or option in this build";
+    }
+    return "unknown status";
+}
+
+pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, void *stream) {
+    if (!ctx_out) return POD_EINVAL;
+    *ctx_out = nullptr;
+    POD_TRY(check_params(p));
+    if (!A_dev) return POD_EINVAL;
+    pod_ctx *c = (pod_ctx *)calloc(1, sizeof(pod_ctx));
+    if (!c) return POD_ENOMEM;
+    c->p = *p;
+    c->A = A_dev;
+    c->stream = (cudaStream_t)stream;
+    c->rmax = p->r > 0 ? p->r : p->k;
+    c->cmax = p->c;
+    c->nmax = c->rmax + c->cmax;
+    c->rtrunc = c->rmax;
+    c->core_f64 = p->core == POD_CORE_F64 || (p->core == POD_CORE_AUTO && p->dtype == POD_F64);
+    c->sms = device_sms();
+    c->plan = tall_plan(p->dtype, p->m, c->rmax, c->cmax, c->sms);
+    c->aplan = atu_plan(p->dtype, p->m, p->n, c->rmax, c->sms);
+    if (core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) > 220 * 1024 ||
+        small_chol_smem(c->cmax) > 220 * 1024 || c->plan.smem[0] > 220 * 1024) {
+        free(c);
+        return POD_EUNSUPPORTED;
+    }
+    const size_t es = p->dtype == POD_F32 ? 4 : 8;
+    const int64_t m = p->m, n = p->n;
+    const int rm = c->rmax, cm = c->cmax, nm = c->nmax;
+    pod_status st = POD_OK;
+#define ALLOC(ptr, cnt) if (st == POD_OK) st = dalloc(&(ptr), (size_t)(cnt))
+    unsigned char *Ub = nullptr;
+    ALLOC(Ub, (size_t)m * rm * es);
+    c->U = Ub;
+    ALLOC(c->sigma, rm);
+    ALLOC(c->s, n);
+    ALLOC(c->ort, n);
+    ALLOC(c->Y, (size_t)n * rm);
+    ALLOC(c->mask, n);
+    ALLOC(c->flags, n);
+    ALLOC(c->w, n);
+    ALLOC(c->cdf, n);
+    ALLOC(c->draws, cm);
+    ALLOC(c->idx, cm);
+    ALLOC(c->hist_idx, (size_t)(n + 1) * cm);
+    ALLOC(c->hist_g, n + 1);
+    ALLOC(c->hist_measure, n + 1);
+    ALLOC(c->st, 1);
+    ALLOC(c->aux, 4);
+    ALLOC(c->part, (size_t)c->plan.grid * ((size_t)rm * cm + (size_t)cm * cm));
+    ALLOC(c->part_atu, (size_t)c->aplan.split * n * rm);
+    ALLOC(c->P, (size_t)rm * cm);
+    ALLOC(c->PG, (size_t)rm * cm + (size_t)cm * cm);
+    ALLOC(c->G2, (size_t)cm * cm);
+    ALLOC(c->Ptot, (size_t)rm * cm);
+    ALLOC(c->M1, (size_t)cm * cm);
+    ALLOC(c->R1p, (size_t)cm * cm);
+    ALLOC(c->E, (size_t)nm * nm + (size_t)cm * cm);
+    ALLOC(c->Xm, (size_t)rm * rm);
+    ALLOC(c->Ym, (size_t)cm * rm);
+    ALLOC(c->rG, (size_t)rm * rm);
+    ALLOC(c->rG2, (size_t)rm * rm);
+    ALLOC(c->rM1, (size_t)rm * rm);
+    ALLOC(c->rR1p, (size_t)rm * rm);
+    ALLOC(c->rsig, rm);
+    ALLOC(c->rVR, (size_t)rm * rm);
+    ALLOC(c->rK, (size_t)rm * rm);
+    ALLOC(c->dots, rm);
+    c->sign_grid = 2 * c->sms;
+    ALLOC(c->part_sign, (size_t)c->sign_grid * rm);
+#undef ALLOC
+    if (st == POD_OK && cudaMallocHost((void **)&c->hstate, sizeof(DevState)) != cudaSuccess) {
+        cudaGetLastError();
+        st = POD_ENOMEM;
+    }
+    if (st != POD_OK) {
+        ctx_free(c);
+        return st;
+    }
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->U, 0, (size_t)m * rm * es, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sigma, 0, rm * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->mask, 1, n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ort, 0, n * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->part, 0, (size_t)c->plan.grid * ((size_t)rm * cm + (size_t)cm * cm) * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->P, 0, (size_t)rm * cm * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->PG, 0, ((size_t)rm * cm + (size_t)cm * cm) * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_g, 0, (n + 1) * sizeof(int32_t), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx_free(c);
+        return POD_ECUDA;
+    }
+    k_set_state<<<1, 32, 0, s>>>(c->st, 0, 0, 0, 0, (int)n);
+    mark(c);
+    pod_status ls = launch_colnorms(A_dev, p->dtype, m, n, p->lda, c->s, s);
+    mark(c);
+    if (ls == POD_OK && cudaGetLastError() != cudaSuccess) ls = POD_ECUDA;
+    if (ls != POD_OK) {
+        ctx_free(c);
+        return ls;
+    }
+    memset(c->hstate, 0, sizeof(DevState));
+    c->hstate->remaining = (int)n;
+    *ctx_out = c;
+    return POD_OK;
+}
+
+pod_status pod_iterate(pod_ctx *c, int32_t max_steps, int32_t *done, double *sin_max, int32_t *steps_run) {
+    if (!c) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (max_steps <= 0) return POD_EINVAL;
+    if (c->refined) return POD_ESTATE;
+    pod_status st = build_graph(c);
+    if (st != POD_OK) return st;
+    const int before = c->hstate->rounds_run;
+    int launched = 0;
+    while (launched < max_steps && !c->hstate->done) {
+        int chunk = (c->hstate->remaining + c->p.c - 1) / c->p.c;
+        if (chunk < 1) chunk = 1;
+        if (chunk > 64) chunk = 64;
+        if (chunk > max_steps - launched) chunk = max_steps - launched;
+        for (int i = 0; i < chunk; ++i) {
+            if (c->graph_ready) {
+                if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    c->poisoned = true;
+                    return POD_ECUDA;
+                }
+                c->launches += c->graph_kernels;
+            } else {
+                st = enqueue_round_any(c);
+                if (st != POD_OK) {
+                    if (st == POD_ECUDA) c->poisoned = true;
+                    return st;
+                }
+            }
+        }
+        launched += chunk;
+        st = read_state(c);
+        if (st != POD_OK) {
+            c->poisoned = true;
+            return st;
+        }
+        if (c->hstate->status != 0) break;
+    }
+    if (done) *done = c->hstate->done;
+    if (sin_max) *sin_max = c->hstate->measure;
+    if (steps_run) *steps_run = c->hstate->rounds_run - before;
+    if (c->hstate->status != 0) return (pod_status)c->hstate->status;
+    return POD_OK;
+}
+
+pod_status pod_modes(pod_ctx *c, void *U_dev, double *sigma_dev, void *V_dev) {
+    if (!c || !U_dev || !sigma_dev) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (V_dev && !c->p.refine) return POD_EINVAL;
+    pod_status st = read_state(c);
+    if (st != POD_OK) {
+        c->poisoned = true;
+        return st;
+    }
+    if (c->p.refine && !c->refined) {
+        st = c->p.dtype == POD_F32 ? run_refine<float>(c) : run_refine<double>(c);
+        if (st != POD_OK) {
+            if (st == POD_ECUDA) c->poisoned = true;
+            return st;
+        }
+    }
+    st = c->p.dtype == POD_F32 ? write_modes<float>(c, U_dev, sigma_dev, V_dev)
+                               : write_modes<double>(c, U_dev, sigma_dev, V_dev);
+    if (st == POD_ECUDA) c->poisoned = true;
+    return st;
+}
+
+pod_status pod_get_trace(pod_ctx *c, int32_t t, int32_t *idx_host, int32_t *g_host, double *measure_host) {
+    if (!c) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    pod_status st = read_state(c);
+    if (st != POD_OK) return st;
+    if (t < 0 || t >= c->hstate->rounds_run) return POD_EINVAL;
+    int32_t g = 0;
+    POD_CUDA_TRY(cudaMemcpy(&g, c->hist_g + t, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (g_host) *g_host = g;
+    if (idx_host && g > 0)
+        POD_CUDA_TRY(cudaMemcpy(idx_host, c->hist_idx + (int64_t)t * c->p.c, g * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost));
+    if (measure_host)
+        POD_CUDA_TRY(cudaMemcpy(measure_host, c->hist_measure + t, sizeof(double), cudaMemcpyDeviceToHost));
+    return POD_OK;
+}
+
+pod_status pod_replay_indices(pod_ctx *c, const int32_t *idx_host, const int32_t *offsets_host, int32_t T) {
+    if (!c || !idx_host || !offsets_host || T < 0 || T > c->p.n) return POD_EINVAL;
+    if (c->graph_ready || c->hstate->rounds_run > 0) return POD_ESTATE;
+    const int32_t total = offsets_host[T];
+    if (offsets_host[0] != 0 || total < 0) return POD_EINVAL;
+    for (int t = 0; t < T; ++t) {
+        const int len = offsets_host[t + 1] - offsets_host[t];
+        if (len < 0 || len > c->p.c) return POD_EINVAL;
+    }
+    for (int i = 0; i < total; ++i)
+        if (idx_host[i] < 0 || idx_host[i] >= c->p.n) return POD_EINVAL;
+    if (c->replay_idx) cudaFree(c->replay_idx);
+    if (c->replay_off) cudaFree(c->replay_off);
+    c->replay_idx = nullptr;
+    c->replay_off = nullptr;
+    POD_TRY(dalloc(&c->replay_idx, total > 0 ? total : 1));
+    POD_TRY(dalloc(&c->replay_off, T + 1));
+    if (total > 0)
+        POD_CUDA_TRY(cudaMemcpy(c->replay_idx, idx_host, total * sizeof(int32_t), cudaMemcpyHostToDevice));
+    POD_CUDA_TRY(cudaMemcpy(c->replay_off, offsets_host, (T + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    c->replay_T = T;
+    return POD_OK;
+}
+
+pod_status pod_backward(pod_ctx *c, const void *dU_dev, const double *dsigma_dev, void *dA_dev,
+                        int32_t accumulate) {
+    (void)dU_dev;
+    (void)dsigma_dev;
+    (void)dA_dev;
+    (void)accumulate;
+    if (!c) return POD_EINVAL;
+    return POD_EUNSUPPORTED;
+}
+
+static pod_status reset_state(pod_ctx *c) {
+    cudaStream_t s = c->stream;
+    const size_t es = c->p.dtype == POD_F32 ? 4 : 8;
+    const int64_t m = c->p.m, n = c->p.n;
+    cudaError_t e = cudaMemsetAsync(c->U, 0, (size_t)m * c->rmax * es, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sigma, 0, c->rmax * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->mask, 1, n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ort, 0, n * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_g, 0, (n + 1) * sizeof(int32_t), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return POD_ECUDA;
+    }
+    k_set_state<<<1, 32, 0, s>>>(c->st, 0, 0, 0, 0, (int)n);
+    mark(c);
+    POD_TRY(launch_colnorms(c->A, c->p.dtype, m, n, c->p.lda, c->s, s));
+    mark(c);
+    memset(c->hstate, 0, sizeof(DevState));
+    c->hstate->remaining = (int)n;
+    c->refined = false;
+    c->refined_r = 0;
+    return POD_OK;
+}
+
+pod_status pod_reset(pod_ctx *c, const void *A_dev) {
+    if (!c) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (A_dev && A_dev != c->A) {
+        c->A = A_dev;
+        if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+        c->graph_ready = false;
+        c->graph_failed = false;
+    }
+    pod_status st = reset_state(c);
+    if (st == POD_ECUDA) c->poisoned = true;
+    return st;
+}
+
+pod_status pod_round_timings(pod_ctx *c, float *ms_host, int32_t cap, int32_t *count) {
+    if (!c || !ms_host || cap <= 0 || !count) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (c->refined) return POD_ESTATE;
+    *count = 0;
+    const int nev = 24;
+    cudaEvent_t ev[nev];
+    for (int i = 0; i < nev; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+            return POD_ECUDA;
+        }
+    c->prof_ev = ev;
+    c->prof_cap = nev;
+    c->prof_n = 1;
+    cudaEventRecord(ev[0], c->stream);
+    pod_status st = enqueue_round_any(c);
+    const int n = c->prof_n;
+    c->prof_ev = nullptr;
+    c->prof_cap = 0;
+    c->prof_n = 0;
+    if (st == POD_OK) st = read_state(c);
+    if (st == POD_OK) {
+        int k = 0;
+        for (int i = 1; i < n && k < cap; ++i, ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+            ms_host[k] = ms;
+        }
+        *count = k;
+    }
+    for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+    if (st == POD_OK && c->hstate->status != 0) st = (pod_status)c->hstate->status;
+    return st;
+}
+
+pod_status pod_counters(pod_ctx *c, int64_t *kernel_launches, int32_t *rounds) {
+    if (!c) return POD_EINVAL;
+    if (kernel_launches) *kernel_launches = c->launches;
+    if (rounds) *rounds = c->hstate->rounds_run;
+    return POD_OK;
+}
+
+void pod_destroy(pod_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    ctx_free(c);
+}
+
+pod_status pod_colnorms(const void *A_dev, int32_t dtype, int64_t m, int64_t n, int64_t lda, double *s_dev,
+                        void *stream) {
+    if (!A_dev || !s_dev || m <= 0 || n <= 0 || lda < m) return POD_EINVAL;
+    if (dtype != POD_F32 && dtype != POD_F64) return POD_EINVAL;
+    return launch_colnorms(A_dev, dtype, m, n, lda, s_dev, (cudaStream_t)stream);
+}
+
+pod_status pod_sample(const uint64_t *w_dev, uint8_t *mask_dev, int64_t n, int32_t c, uint64_t seed, int32_t t,
+                      int32_t stream_id, int32_t *idx_dev, int32_t *g_dev, void *stream) {
+    if (!w_dev || !mask_dev || !idx_dev || !g_dev || n <= 0 || c <= 0 || t < 0 || stream_id < 0)
+        return POD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t *w = nullptr, *cdf = nullptr;
+    uint8_t *flags = nullptr;
+    int32_t *draws = nullptr;
+    POD_CUDA_TRY(cudaMallocAsync((void **)&w, n * sizeof(uint64_t), s));
+    POD_CUDA_TRY(cudaMallocAsync((void **)&cdf, n * sizeof(uint64_t), s));
+    POD_CUDA_TRY(cudaMallocAsync((void **)&flags, n, s));
+    POD_CUDA_TRY(cudaMallocAsync((void **)&draws, c * sizeof(int32_t), s));
+    POD_CUDA_TRY(cudaMemcpyAsync(w, w_dev, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    POD_CUDA_TRY(cudaMemsetAsync(flags, 0, n, s));
+    SampleArgs a{};
+    a.n = n;
+    a.c = c;
+    a.mode_round0 = 3;
+    a.mode = 3;
+    a.seed = seed;
+    a.stream_id = stream_id;
+    a.w = w;
+    a.cdf = cdf;
+    a.mask = mask_dev;
+    a.flags = flags;
+    a.draws = draws;
+    a.idx = idx_dev;
+    a.st = nullptr;
+    a.g_out = g_dev;
+    a.t_fixed = t;
+    pod_status st = launch_sample(a, s);
+    cudaFreeAsync(w, s);
+    cudaFreeAsync(cdf, s);
+    cudaFreeAsync(flags, s);
+    cudaFreeAsync(draws, s);
+    return st;
+}
+
+pod_status pod_block_merge(int32_t dtype, int64_t m, const void *U1_dev, const double *s1_dev, int32_t r1,
+                           const void *C_dev, int64_t ldc, int32_t g, int32_t r, int32_t core, void *U_out_dev,
+                           double *s_out_dev, int32_t *r_out_host, void *stream) {
+    if ((dtype != POD_F32 && dtype != POD_F64) || m <= 0 || r1 < 0 || g < 1 || r < 1 || ldc < m) return POD_EINVAL;
+    if (!C_dev || !U_out_dev || !s_out_dev || !r_out_host || (r1 > 0 && (!U1_dev || !s1_dev))) return POD_EINVAL;
+    if (core < POD_CORE_AUTO || core > POD_CORE_F64) return POD_EINVAL;
+    pod_params p{};
+    p.m = m;
+    p.n = g;
+    p.lda = ldc;
+    p.k = 1;
+    p.c = g;
+    p.r = r > r1 ? r : r1;
+    p.dtype = dtype;
+    p.core = core;
+    p.tol = -1.0;
+    p.col_strategy = POD_UNF;
+    pod_ctx *c = nullptr;
+    pod_status st = pod_init(&c, &p, C_dev, stream);
+    if (st != POD_OK) return st;
+    cudaStream_t s = c->stream;
+    const size_t es = dtype == POD_F32 ? 4 : 8;
+    // state: U1 carried (r1 modes), all g columns drawn this round (replay of 0..g-1)
+    if (r1 > 0) {
+        if (cudaMemcpy2DAsync(c->U, m * es, U1_dev, m * es, m * es, r1, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(c->sigma, s1_dev, r1 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            pod_destroy(c);
+            return POD_ECUDA;
+        }
+    }
+    c->rtrunc = r;   // truncation rank of this merge
+    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)g);
+    int32_t off[2] = {0, g};
+    if (!idx) {
+        pod_destroy(c);
+        return POD_ENOMEM;
+    }
+    for (int j = 0; j < g; ++j) idx[j] = j;
+    st = pod_replay_indices(c, idx, off, 1);
+    free(idx);
+    if (st == POD_OK) {
+        k_set_state<<<1, 32, 0, s>>>(c->st, r1, 0, 0, 0, 1);
+        c->graph_failed = true;   // run eagerly
+        st = enqueue_round_any(c);
+    }
+    if (st == POD_OK) st = read_state(c);
+    if (st == POD_OK && c->hstate->status != 0) st = (pod_status)c->hstate->status;
+    if (st == POD_OK) {
+        const int rn = c->hstate->r_cur;
+        *r_out_host = rn;
+        if (cudaMemcpyAsync(U_out_dev, c->U, (size_t)m * rn * es, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(s_out_dev, c->sigma, rn * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            st = POD_ECUDA;
+        }
+    }
+    pod_destroy(c);
+    return st;
+}
+
+}  // extern "C"

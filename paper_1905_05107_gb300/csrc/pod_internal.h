@@ -1,0 +1,150 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include "common.cuh"
+
+// ---------------------------------------------------------------- sampler.cu
+struct SampleArgs {
+    int64_t n;
+    int c;
+    int L;                     // weight bits
+    int mode_round0, mode;     // value source for round 0 and later rounds
+    uint64_t seed;
+    int stream_id;
+    const double *s;           // column squared norms
+    const double *ort;         // ORT values
+    uint64_t *w;               // n weights (scratch, or input for mode 3)
+    uint64_t *cdf;             // n prefix sums (scratch)
+    uint8_t *mask;             // n, S membership
+    uint8_t *flags;            // n scratch, zero on entry and on exit
+    int32_t *draws;            // c raw draws
+    int32_t *idx;              // c sorted distinct
+    DevState *st;              // nullptr for the stand-alone entry point
+    int32_t *g_out;            // stand-alone: distinct count
+    int t_fixed;               // stand-alone: round index
+    // replay of frozen index lists
+    const int32_t *replay_idx;
+    const int32_t *replay_off;
+    int replay_T;
+    // history
+    int32_t *hist_idx;
+    int32_t *hist_g;
+};
+pod_status launch_sample(const SampleArgs &a, cudaStream_t st);
+pod_status launch_colnorms(const void *A, int dtype, int64_t m, int64_t n, int64_t lda,
+                           double *s, cudaStream_t st);
+pod_status launch_ort_values(const double *s, const double *Y, int64_t n, int ldy,
+                             const DevState *st, const uint8_t *mask, double *ort,
+                             cudaStream_t stream);
+int weight_bits(int64_t n);
+
+// ------------------------------------------------------------------- tall.cu
+// Operands of the tall-skinny passes.  C columns are A + (idx ? idx[j] : j) * lda.
+// Sizes are read on the device: r = st->r_cur (columns of U), g = st->g
+// (columns of C), rn = st->r_new (columns written by the update).
+template <typename T>
+struct TallArgs {
+    int64_t m;
+    const T *A;
+    int64_t lda;
+    const int32_t *idx;
+    T *U;
+    int64_t ldu;
+    const DevState *st;
+    int rmax, cmax;         // capacities (layout)
+    int bm;                 // rows per slab
+    double *part;           // partials [gridDim.x][part_stride]
+    int64_t part_stride;
+    const double *P;        // r x g, ld cmax
+    const double *P2;       // r x g, ld cmax
+    const double *M1;       // g x g, ld cmax (upper triangular)
+    const double *Xm;       // r x rn, ld rmax
+    const double *Ym;       // g x rn, ld rmax
+};
+
+enum TallKind { TALL_PROJ = 0, TALL_CGS = 1, TALL_QR2 = 2, TALL_UPDATE = 3 };
+
+struct TallPlan {
+    int grid;
+    int bm;
+    size_t smem[4];
+};
+
+TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms);
+template <typename T>
+pod_status launch_tall(TallKind kind, const TallArgs<T> &a, const TallPlan &plan, cudaStream_t st);
+
+// Y = A^T U (n x r, column-major with leading dimension n), optionally only
+// for columns in `mask`.  Partials over `split` row ranges, reduced by the
+// caller with launch_reduce.
+template <typename T>
+struct AtuArgs {
+    int64_t m, n;
+    const T *A;
+    int64_t lda;
+    const T *U;
+    int64_t ldu;
+    const DevState *st;     // r = st->r_cur
+    const uint8_t *mask;    // may be null
+    int rmax;               // partial stride is n * rmax
+    int ldy;                // unused (Y is column-major, ld n)
+    double *part;           // [split][n * r], column l at l * n
+};
+struct AtuPlan {
+    int nb, split, bm;
+    size_t smem;
+    dim3 grid;
+};
+AtuPlan atu_plan(int dtype, int64_t m, int64_t n, int rmax, int num_sms);
+template <typename T>
+pod_status launch_atu(const AtuArgs<T> &a, const AtuPlan &plan, cudaStream_t st);
+
+// d_l = sum_i U_il z_i with z_i = int32(Philox(i, 0, 3, 0).x0) / 2^31.
+template <typename T>
+pod_status launch_sign_dots(const T *U, int64_t m, int64_t ldu, int r, uint64_t seed,
+                            double *part, int grid, cudaStream_t st);
+
+// ------------------------------------------------------------------ small.cu
+pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t count,
+                         double *out, const DevState *st, cudaStream_t s);
+
+struct SmallArgs {
+    DevState *st;
+    int dtype;              // storage type (rounding of coefficients)
+    int core_f64;           // arithmetic of the core SVD
+    int64_t m;
+    int k, r, c, rmax, cmax;   // r: truncation rank (<= rmax, the layout capacity)
+    int criterion;
+    double tol;
+    int max_iter;
+    double *sigma;          // r_cur values (in) / r_new values (out)
+    const double *P;        // r x g (ld cmax): U^T C
+    const double *PG;       // cgs partial sums: P2 (r x g, ld cmax) then G (g x g, ld cmax)
+    const double *G2;       // second CholeskyQR Gram (g x g, ld cmax)
+    double *Ptot;           // r x g, ld cmax
+    double *M1;             // g x g, ld cmax
+    double *R1p;            // g x g, ld cmax
+    double *E;              // nc x nc scratch (column-major, ld rmax + cmax)
+    double *Xm;             // r x rn, ld rmax
+    double *Ym;             // g x rn, ld rmax
+    double *hist_measure;   // per-round measure
+};
+pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s);
+pod_status launch_core(const SmallArgs &a, cudaStream_t s);
+size_t core_smem_bytes(int rmax, int cmax, int dtype);
+size_t small_chol_smem(int cmax);
+pod_status launch_finish(DevState *st, cudaStream_t s);
+
+// refinement QR(A^T U), SVD(R)
+struct RefineArgs {
+    int r;                  // modes
+    int dtype;
+    const double *G;        // r x r, ld r: Y^T Y
+    const double *G2;       // r x r, ld r: second CholeskyQR Gram
+    double *M1, *R1p;       // r x r, ld r
+    double *sigma;          // out: r
+    double *VR;             // out: r x r (ld r), U <- U VR
+    double *K;              // out: r x r (ld r), V <- Y K
+};
+pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s);
+pod_status launch_refine_svd(const RefineArgs &a, cudaStream_t s);
