@@ -279,10 +279,14 @@ def run_ours(args):
         ctx.reset()
         per = {}
         rg = []
+        sweeps, core_cyc = [], []
         for t in range(rounds):
             for kname, v in ctx.round_timings().items():
                 per.setdefault(kname, []).append(v)
             rg.append(len(ctx.trace(t)[0]))
+            sw, cyc = ctx.core_stats()
+            sweeps.append(sw)
+            core_cyc.append(cyc)
         ctx.modes()
         cn = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         torch.cuda.synchronize()
@@ -326,6 +330,7 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms,
                 "time_share": {k: round(totals[k] / sum(totals.values()), 4) for k in totals},
                 "dominant_kernel": dominant}
+    core_phase = np.mean(np.array(core_cyc, dtype=np.float64), axis=0).tolist() if core_cyc else []
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -344,6 +349,11 @@ def run_ours(args):
                 "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(m * n * es),
                         "d2h_bytes_per_step": int(m * K_MODES * 4 + K_MODES * 8)},
                 "gpu_launches": int(launches),
+                "core_svd": {"jacobi_sweeps_mean": float(np.mean(sweeps)) if sweeps else None,
+                             "jacobi_sweeps_max": int(np.max(sweeps)) if sweeps else None,
+                             "phase_cycles_mean": {k: round(v) for k, v in zip(
+                                 ["chol2_and_E", "jacobi", "finish", "convergence", "coefficients", "total"],
+                                 core_phase)}},
                 "roofline": roofline,
                 "clocks": clk,
                 "cpu_baseline": cpu}

@@ -177,9 +177,10 @@ POD_API pod_status pod_reset(pod_ctx *ctx, const void *A_dev);
  * pod_round_timings -- run the next ISMA round (as pod_iterate with
  * max_steps = 1 would) launch by launch, with a CUDA event recorded on the
  * context's stream after every kernel, and return each kernel's duration in
- * milliseconds in launch order (probabilities, draws, U^T C, its sum,
- * C - U P with U^T Z and Z^T Z, its sum, first Cholesky, second CholeskyQR
- * Gram, its sum, core SVD, update, end of round).  Synchronises.
+ * milliseconds in launch order (with ORT: A^T U, ORT values; then
+ * probabilities and draws, U^T C, C - U P with U^T Z and Z^T Z, first
+ * Cholesky, second CholeskyQR Gram, core SVD, update, end of round).
+ * Synchronises.
  *   ms_host : capacity cap floats;  count : entries written.
  */
 POD_API pod_status pod_round_timings(pod_ctx *ctx, float *ms_host, int32_t cap, int32_t *count);
@@ -190,6 +191,16 @@ POD_API pod_status pod_round_timings(pod_ctx *ctx, float *ms_host, int32_t cap, 
  * synchronisation.  Host-only, never synchronises.
  */
 POD_API pod_status pod_counters(pod_ctx *ctx, int64_t *kernel_launches, int32_t *rounds);
+
+/*
+ * pod_core_stats -- diagnostics of the last core SVD of E (Algorithm 2):
+ * Jacobi sweeps run, and SM clock cycles spent in its phases
+ * (cycles[0] second CholeskyQR factor and E, [1] Jacobi sweeps, [2] top-r
+ * vectors and singular values, [3] convergence measure, [4] update
+ * coefficients, [5] whole kernel).  Synchronises.  Either pointer may be
+ * NULL.
+ */
+POD_API pod_status pod_core_stats(pod_ctx *ctx, int32_t *sweeps, int64_t *cycles);
 
 /* pod_destroy -- free every workspace of ctx (NULL is a no-op). Synchronises. */
 POD_API void pod_destroy(pod_ctx *ctx);

@@ -100,7 +100,9 @@ struct pod_ctx {
     double *hist_measure;
     DevState *st, *aux;
     double *part, *part_atu;
-    double *P, *PG, *G2, *Ptot, *M1, *R1p, *E, *Xm, *Ym;
+    double *P, *PG, *G2, *Ptot, *M1, *R1p, *E, *Xm, *Ym, *gsum;
+    unsigned *counters, *atu_counters;
+    int vec;            // 16-byte copies legal for A and U
     double *rG, *rG2, *rM1, *rR1p, *rsig, *rVR, *rK, *dots, *part_sign;
     int32_t *replay_idx, *replay_off;
     int replay_T;
@@ -131,7 +133,7 @@ static void ctx_free(pod_ctx *c) {
                     c->idx, c->hist_idx, c->hist_g, c->hist_measure, c->st, c->aux, c->part,
                     c->part_atu, c->P, c->PG, c->G2, c->Ptot, c->M1, c->R1p, c->E, c->Xm, c->Ym,
                     c->rG, c->rG2, c->rM1, c->rR1p, c->rsig, c->rVR, c->rK, c->dots, c->part_sign,
-                    c->replay_idx, c->replay_off};
+                    c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->hstate) cudaFreeHost(c->hstate);
@@ -151,6 +153,7 @@ static pod_status check_params(const pod_params *p) {
     if (p->criterion != POD_SUBSPACE && p->criterion != POD_MODES) return POD_EINVAL;
     if (p->core < POD_CORE_AUTO || p->core > POD_CORE_F64) return POD_EINVAL;
     if (p->rows != 0) return POD_EUNSUPPORTED;
+    if (p->c > 256 || (p->r > 0 ? p->r : p->k) > 256) return POD_EUNSUPPORTED;
     if (!(p->tol == p->tol)) return POD_EINVAL;
     return POD_OK;
 }
@@ -170,6 +173,10 @@ static TallArgs<T> tall_args(pod_ctx *c, double *part, int64_t stride) {
     a.bm = c->plan.bm;
     a.part = part;
     a.part_stride = stride;
+    a.gsum = c->gsum;
+    a.counters = c->counters;
+    a.vec = c->vec;
+    a.out = nullptr;
     a.P = c->P;
     a.P2 = c->PG;
     a.M1 = c->M1;
@@ -225,10 +232,10 @@ static pod_status enqueue_round(pod_ctx *c) {
         aa.ldy = (int)c->p.n;
         aa.rmax = c->rmax;
         aa.part = c->part_atu;
+        aa.Y = c->Y;
+        aa.counters = c->atu_counters;
+        aa.vec = c->vec;
         POD_TRY(launch_atu<T>(aa, c->aplan, s));
-        mark(c);
-        POD_TRY(launch_reduce(c->part_atu, c->aplan.split, (int64_t)c->p.n * c->rmax,
-                              (int64_t)c->p.n * c->rmax, c->Y, c->st, s));
         mark(c);
         POD_TRY(launch_ort_values(c->s, c->Y, c->p.n, (int)c->p.n, c->st, c->mask, c->ort, s));
         mark(c);
@@ -259,26 +266,19 @@ static pod_status enqueue_round(pod_ctx *c) {
     mark(c);
 
     TallArgs<T> ta = tall_args<T>(c, c->part, (int64_t)c->rmax * c->cmax);
+    ta.out = c->P;
     POD_TRY(launch_tall<T>(TALL_PROJ, ta, c->plan, s));
     mark(c);
-    POD_TRY(launch_reduce(c->part, c->plan.grid, ta.part_stride, ta.part_stride, c->P, c->st, s));
-    mark(c);
     ta.part_stride = sPG;
-    ta.P = c->P;
+    ta.out = c->PG;
     POD_TRY(launch_tall<T>(TALL_CGS, ta, c->plan, s));
-    mark(c);
-    POD_TRY(launch_reduce(c->part, c->plan.grid, sPG, sPG, c->PG, c->st, s));
     mark(c);
     SmallArgs sm = small_args(c);
     POD_TRY(launch_small_chol(sm, s));
     mark(c);
     ta.part_stride = (int64_t)c->cmax * c->cmax;
-    ta.P = c->P;
-    ta.P2 = c->PG;
-    ta.M1 = c->M1;
+    ta.out = c->G2;
     POD_TRY(launch_tall<T>(TALL_QR2, ta, c->plan, s));
-    mark(c);
-    POD_TRY(launch_reduce(c->part, c->plan.grid, ta.part_stride, ta.part_stride, c->G2, c->st, s));
     mark(c);
     POD_TRY(launch_core(sm, s));
     mark(c);
@@ -350,9 +350,11 @@ static pod_status run_refine(pod_ctx *c) {
     aa.ldy = (int)n;
     aa.rmax = c->rmax;
     aa.part = c->part_atu;
+    aa.Y = c->Y;
+    aa.counters = c->atu_counters;
+    aa.vec = c->vec;
     POD_TRY(launch_atu<T>(aa, c->aplan, s));
-    POD_TRY(launch_reduce(c->part_atu, c->aplan.split, n * c->rmax, n * r, c->Y, nullptr, s));
-    c->launches += 2;
+    c->launches += 1;
     // G = Y^T Y, CholeskyQR2 on the n x r matrix Y (FP64 tall passes)
     TallPlan yplan = tall_plan(POD_F64, n, r, r, c->sms);
     TallArgs<double> ya{};
@@ -367,14 +369,20 @@ static pod_status run_refine(pod_ctx *c) {
     ya.bm = yplan.bm;
     ya.part = c->part;
     ya.part_stride = (int64_t)r * r;
-    if ((size_t)yplan.grid * r * r > (size_t)c->plan.grid * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax))
+    ya.gsum = c->gsum;
+    ya.counters = c->counters;
+    ya.vec = (n % 2) == 0;
+    const size_t part_cap = (size_t)c->plan.grid * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax);
+    const size_t gsum_cap = (size_t)(c->plan.groups + 1) * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax);
+    if ((size_t)yplan.grid * r * r > part_cap || (size_t)(yplan.groups + 1) * r * r > gsum_cap ||
+        yplan.groups + 1 > 64 + c->plan.groups)
         return POD_EUNSUPPORTED;
     k_set_state<<<1, 32, 0, s>>>(c->aux + 1, r, r, 0, 1, 1);
     c->launches += 1;
     ya.st = c->aux + 1;
+    ya.out = c->rG;
     POD_TRY(launch_tall<double>(TALL_PROJ, ya, yplan, s));
-    POD_TRY(launch_reduce(c->part, yplan.grid, (int64_t)r * r, (int64_t)r * r, c->rG, nullptr, s));
-    c->launches += 2;
+    c->launches += 1;
     RefineArgs ra{};
     ra.r = r;
     ra.dtype = c->p.dtype;
@@ -391,9 +399,9 @@ static pod_status run_refine(pod_ctx *c) {
     c->launches += 1;
     ya.st = c->aux + 2;
     ya.M1 = c->rM1;
+    ya.out = c->rG2;
     POD_TRY(launch_tall<double>(TALL_QR2, ya, yplan, s));
-    POD_TRY(launch_reduce(c->part, yplan.grid, (int64_t)r * r, (int64_t)r * r, c->rG2, nullptr, s));
-    c->launches += 2;
+    c->launches += 1;
     POD_TRY(launch_refine_svd(ra, s));
     c->launches += 1;
     // U <- U V_R (in place)
@@ -477,8 +485,12 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     c->sms = device_sms();
     c->plan = tall_plan(p->dtype, p->m, c->rmax, c->cmax, c->sms);
     c->aplan = atu_plan(p->dtype, p->m, p->n, c->rmax, c->sms);
+    {
+        const size_t esz = p->dtype == POD_F32 ? 4 : 8;
+        c->vec = ((uintptr_t)A_dev % 16 == 0) && ((p->lda * esz) % 16 == 0) && ((p->m * esz) % 16 == 0);
+    }
     if (core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) > 220 * 1024 ||
-        small_chol_smem(c->cmax) > 220 * 1024 || c->plan.smem[0] > 220 * 1024) {
+        small_chol_smem(c->cmax) > 220 * 1024 || c->plan.smem > 227 * 1024) {
         free(c);
         return POD_EUNSUPPORTED;
     }
@@ -508,6 +520,9 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     ALLOC(c->part, (size_t)c->plan.grid * ((size_t)rm * cm + (size_t)cm * cm));
     ALLOC(c->part_atu, (size_t)c->aplan.split * n * rm);
     ALLOC(c->P, (size_t)rm * cm);
+    ALLOC(c->gsum, (size_t)(c->plan.groups + 1) * ((size_t)rm * cm + (size_t)cm * cm));
+    ALLOC(c->counters, 64 + c->plan.groups);
+    ALLOC(c->atu_counters, (size_t)c->aplan.grid.x + 64);
     ALLOC(c->PG, (size_t)rm * cm + (size_t)cm * cm);
     ALLOC(c->G2, (size_t)cm * cm);
     ALLOC(c->Ptot, (size_t)rm * cm);
@@ -546,6 +561,8 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (e == cudaSuccess) e = cudaMemsetAsync(c->P, 0, (size_t)rm * cm * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->PG, 0, ((size_t)rm * cm + (size_t)cm * cm) * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_g, 0, (n + 1) * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, (64 + c->plan.groups) * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->atu_counters, 0, (c->aplan.grid.x + 64) * sizeof(unsigned), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ctx_free(c);
@@ -757,6 +774,17 @@ pod_status pod_round_timings(pod_ctx *c, float *ms_host, int32_t cap, int32_t *c
     for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
     if (st == POD_OK && c->hstate->status != 0) st = (pod_status)c->hstate->status;
     return st;
+}
+
+pod_status pod_core_stats(pod_ctx *c, int32_t *sweeps, int64_t *cycles) {
+    if (!c) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    pod_status st = read_state(c);
+    if (st != POD_OK) return st;
+    if (sweeps) *sweeps = c->hstate->sweeps;
+    if (cycles)
+        for (int i = 0; i < 6; ++i) cycles[i] = c->hstate->core_cycles[i];
+    return POD_OK;
 }
 
 pod_status pod_counters(pod_ctx *c, int64_t *kernel_launches, int32_t *rounds) {

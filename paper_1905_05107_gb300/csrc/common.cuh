@@ -26,10 +26,11 @@ struct DevState {
     int r_new;      // modes kept by this round's merge
     int rounds_run; // rounds completed
     int done_next;  // stop decision of the current round, applied at its end
-    int pad_;
+    int sweeps;     // Jacobi sweeps of the last core SVD
     double measure; // last convergence measure
     double sin_max;
     double cos_min;
+    long long core_cycles[6];   // last core SVD: clock64 deltas of its phases
 };
 
 // ---------------------------------------------------------------------------
@@ -155,14 +156,14 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
     e = fmaf(a.lo, b.hi, e);
     return df_fast_two_sum(p, e);
 }
+// a / b: approximate quotient q1 (2 ulp), then one correction from the exact
+// residual a - b q1, giving ~2^-44 relative accuracy without IEEE division.
 __device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) {
-    float q1 = a.hi / b.hi;
-    dfloat r = a - b * dfloat{q1, 0.f};
-    float q2 = r.hi / b.hi;
-    r = r - b * dfloat{q2, 0.f};
-    float q3 = r.hi / b.hi;
-    dfloat q = df_fast_two_sum(q1, q2);
-    return q + dfloat{q3, 0.f};
+    const float rb = __frcp_rn(b.hi);
+    const float q1 = a.hi * rb;
+    const dfloat r = a - b * dfloat{q1, 0.f};
+    const float q2 = r.hi * rb;
+    return df_fast_two_sum(q1, q2);
 }
 
 // Scalar traits: the small dense algebra is written once over X = double
@@ -170,6 +171,7 @@ __device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) {
 template <typename X> struct XOps;
 template <> struct XOps<double> {
     __device__ static double from(double d) { return d; }
+    __device__ static double from_f(float f) { return (double)f; }
     __device__ static double to(double x) { return x; }
     __device__ static double sqrt_(double x) { return sqrt(x); }
     __device__ static double zero() { return 0.0; }
@@ -180,14 +182,14 @@ template <> struct XOps<dfloat> {
         float hi = (float)d;
         return {hi, (float)(d - (double)hi)};
     }
+    __device__ static dfloat from_f(float f) { return {f, 0.f}; }
     __device__ static double to(dfloat x) { return (double)x.hi + (double)x.lo; }
     __device__ static dfloat sqrt_(dfloat a) {
         if (!(a.hi > 0.f)) return {0.f, 0.f};
-        float s = sqrtf(a.hi);
-        dfloat s2 = dfloat{s, 0.f} * dfloat{s, 0.f};
-        dfloat r = a - s2;
-        float c = r.hi / (2.f * s);
-        return df_fast_two_sum(s, c);
+        const float rs = rsqrtf(a.hi);
+        const float s = a.hi * rs;                       // sqrt(a.hi), ~2 ulp
+        const dfloat r = a - dfloat{s, 0.f} * dfloat{s, 0.f};
+        return df_fast_two_sum(s, 0.5f * r.hi * rs);     // one Newton step from the exact residual
     }
     __device__ static dfloat zero() { return {0.f, 0.f}; }
     __device__ static dfloat one() { return {1.f, 0.f}; }
@@ -199,6 +201,14 @@ __device__ __forceinline__ bool x_gt(dfloat a, dfloat b) {
 }
 __device__ __forceinline__ float x_hi(double a) { return (float)a; }
 __device__ __forceinline__ float x_hi(dfloat a) { return a.hi; }
+// Rotation arithmetic of the Jacobi sweeps: fast reciprocals on the FP32
+// path (a rotation need not be exact, only applied consistently to the
+// columns and to V), IEEE on the FP64 path.
+__device__ __forceinline__ float j_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double j_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float j_rsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double j_rsqrt(double a) { return 1.0 / sqrt(a); }
+
 __device__ __forceinline__ double x_shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ dfloat x_shfl_xor(dfloat v, int o) {
     return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};

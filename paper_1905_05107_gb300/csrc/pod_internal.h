@@ -55,6 +55,10 @@ struct TallArgs {
     int bm;                 // rows per slab
     double *part;           // partials [gridDim.x][part_stride]
     int64_t part_stride;
+    double *gsum;           // group sums [ceil(grid / 16)][part_stride]
+    double *out;            // final sum (part_stride doubles)
+    unsigned *counters;     // arrival counters (ceil(grid / 16) + 1), zero between launches
+    int vec;                // 1: 16-byte copies are legal for every operand
     const double *P;        // r x g, ld cmax
     const double *P2;       // r x g, ld cmax
     const double *M1;       // g x g, ld cmax (upper triangular)
@@ -67,7 +71,8 @@ enum TallKind { TALL_PROJ = 0, TALL_CGS = 1, TALL_QR2 = 2, TALL_UPDATE = 3 };
 struct TallPlan {
     int grid;
     int bm;
-    size_t smem[4];
+    int groups;
+    size_t smem;
 };
 
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms);
@@ -89,6 +94,9 @@ struct AtuArgs {
     int rmax;               // partial stride is n * rmax
     int ldy;                // unused (Y is column-major, ld n)
     double *part;           // [split][n * r], column l at l * n
+    double *Y;              // result, column-major n x r (ld n)
+    unsigned *counters;     // one per column block, zero between launches
+    int vec;                // 1: 16-byte copies are legal
 };
 struct AtuPlan {
     int nb, split, bm;

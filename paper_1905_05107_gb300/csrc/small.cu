@@ -25,161 +25,210 @@ __device__ __forceinline__ double round_to(int dtype, double v) {
 }
 
 // ---------------------------------------------------------------------------
-// In-place upper Cholesky with pivot dropping.  On entry the upper triangle
-// of W (n x n, ld) holds a symmetric Gram matrix; on exit W holds R with
-// R^T R = G on the kept indices.  A pivot d <= thr marks its index as
-// numerically dependent: R's row is zero (Algorithm 2 drops the matching
-// zero singular values of E).
+// Upper Cholesky with pivot dropping, one barrier per pivot.  W (n x n, ld)
+// holds a symmetric Gram matrix in its upper triangle and is overwritten;
+// R (ld) receives the factor with R^T R = G on the kept indices.  A pivot
+// d <= thr marks its index as numerically dependent: R's row is zero
+// (Algorithm 2 drops the matching zero singular values of E).  The row of
+// pivot k is written to R while the trailing update reads the unscaled row
+// from W, so both happen in the same phase.
 // ---------------------------------------------------------------------------
 template <typename X>
-__device__ void chol_drop(X *W, int ld, int n, X thr, X *s_piv) {
+__device__ void chol_drop(X *W, int ldw, int n, X thr, X *R, int ldr, X *piv3) {
     const int tid = threadIdx.x, bd = blockDim.x;
+    for (int e = tid; e < n * n; e += bd) {
+        const int i = e / n, j = e % n;
+        if (i > j) R[i * ldr + j] = XOps<X>::zero();
+    }
+    // piv3 = {sqrt(d), 1/sqrt(d), 1/d} of the current pivot (zeros if dropped),
+    // written by the thread that produces the pivot's final value
+    auto set_pivot = [&](X d) {
+        if (x_gt(d, thr)) {
+            const X p = XOps<X>::sqrt_(d);
+            piv3[0] = p;
+            piv3[1] = XOps<X>::one() / p;
+            piv3[2] = XOps<X>::one() / d;
+        } else {
+            piv3[0] = piv3[1] = piv3[2] = XOps<X>::zero();
+        }
+    };
+    if (tid == 0 && n > 0) set_pivot(W[0]);
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
-        if (tid == 0) {
-            X d = W[k * ld + k];
-            *s_piv = x_gt(d, thr) ? XOps<X>::sqrt_(d) : XOps<X>::zero();
-        }
-        __syncthreads();
-        const X piv = *s_piv;
+        const X piv = piv3[0], inv_piv = piv3[1], inv_d = piv3[2];
         const bool keep = x_hi(piv) > 0.f;
-        for (int j = k + tid; j < n; j += bd) {
-            X v = XOps<X>::zero();
-            if (keep) v = (j == k) ? piv : W[k * ld + j] / piv;
-            W[k * ld + j] = v;
-        }
-        __syncthreads();
-        if (keep) {
-            const int w = n - k - 1;
-            for (int e = tid; e < w * w; e += bd) {
-                const int i = k + 1 + e / w, j = k + 1 + e % w;
-                if (i <= j) W[i * ld + j] = W[i * ld + j] - W[k * ld + i] * W[k * ld + j];
+        const int rowlen = n - k, w = n - k - 1;
+        X next_d = XOps<X>::zero();
+        bool owner = false;
+        for (int e = tid; e < rowlen + (keep ? w * w : 0); e += bd) {
+            if (e < rowlen) {
+                const int j = k + e;
+                R[k * ldr + j] = keep ? (j == k ? piv : W[k * ldw + j] * inv_piv) : XOps<X>::zero();
+            } else {
+                const int e2 = e - rowlen;
+                const int i = k + 1 + e2 / w, j = k + 1 + e2 % w;
+                if (i <= j) {
+                    const X v = W[i * ldw + j] - (W[k * ldw + i] * W[k * ldw + j]) * inv_d;
+                    W[i * ldw + j] = v;
+                    if (i == k + 1 && j == k + 1) {
+                        next_d = v;
+                        owner = true;
+                    }
+                }
             }
         }
         __syncthreads();
+        if (k + 1 < n) {
+            // the next pivot: updated above, or unchanged when this pivot was dropped
+            if (keep ? owner : tid == 0) set_pivot(keep ? next_d : W[(k + 1) * ldw + k + 1]);
+            __syncthreads();
+        }
     }
-    for (int e = tid; e < n * n; e += bd) {
-        const int i = e / n, j = e % n;
-        if (i > j) W[i * ld + j] = XOps<X>::zero();
-    }
-    __syncthreads();
 }
 
-// M = R^{-1} for upper triangular R (zero rows of dropped indices give zero
-// rows and columns of M).  Row-oriented back substitution: M starts as I.
+// M = R^{-1} for upper triangular R, one barrier per row (zero pivots of
+// dropped indices give zero rows and columns of M).  Mw is a work array;
+// row k of M is the scaled row k of Mw, written while the rows above are
+// updated from the unscaled row.
 template <typename X>
-__device__ void tri_inv(const X *R, int ldr, int n, X *M, int ldm) {
+__device__ void tri_inv(const X *R, int ldr, int n, X *Mw, int ldw, X *M, int ldm, X *dinv) {
     const int tid = threadIdx.x, bd = blockDim.x;
     for (int e = tid; e < n * n; e += bd) {
         const int i = e / n, j = e % n;
-        M[i * ldm + j] = (i == j && x_hi(R[i * ldr + i]) != 0.f) ? XOps<X>::one() : XOps<X>::zero();
+        Mw[i * ldw + j] = (i == j) ? XOps<X>::one() : XOps<X>::zero();
+        M[i * ldm + j] = XOps<X>::zero();
+    }
+    for (int k = tid; k < n; k += bd) {
+        const X d = R[k * ldr + k];
+        dinv[k] = x_hi(d) != 0.f ? XOps<X>::one() / d : XOps<X>::zero();
     }
     __syncthreads();
     for (int k = n - 1; k >= 0; --k) {
-        const X d = R[k * ldr + k];
-        if (x_hi(d) != 0.f) {
-            for (int j = k + tid; j < n; j += bd) M[k * ldm + j] = M[k * ldm + j] / d;
-            __syncthreads();
-            for (int e = tid; e < k * (n - k); e += bd) {
-                const int i = e / (n - k), j = k + e % (n - k);
-                M[i * ldm + j] = M[i * ldm + j] - R[i * ldr + k] * M[k * ldm + j];
+        const X inv = dinv[k];
+        if (x_hi(inv) != 0.f) {
+            const int w = n - k;
+            for (int e = tid; e < w * (k + 1); e += bd) {
+                const int i = e / w, j = k + e % w;
+                if (i == k) M[k * ldm + j] = Mw[k * ldw + j] * inv;
+                else Mw[i * ldw + j] = Mw[i * ldw + j] - R[i * ldr + k] * (Mw[k * ldw + j] * inv);
             }
         }
         __syncthreads();
     }
 }
 
-// A <- A B for upper triangular A, B (in place in A; columns descending).
+// C = A B for upper triangular A, B (all entries in parallel).
 template <typename X>
-__device__ void trmm_inplace_left(X *A, int lda, const X *B, int ldb, int n) {
-    const int tid = threadIdx.x, bd = blockDim.x;
-    for (int j = n - 1; j >= 0; --j) {
-        for (int i = tid; i <= j; i += bd) {
-            X s = XOps<X>::zero();
-            for (int l = i; l <= j; ++l) s = s + A[i * lda + l] * B[l * ldb + j];
-            A[i * lda + j] = s;
-        }
-        __syncthreads();
+__device__ void trmm_upper(const X *A, int lda, const X *B, int ldb, int n, X *C, int ldc) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        X s = XOps<X>::zero();
+        for (int l = i; l <= j; ++l) s = s + A[i * lda + l] * B[l * ldb + j];
+        C[i * ldc + j] = s;
     }
-}
-
-// B <- A B for upper triangular A, B (in place in B; rows ascending).
-template <typename X>
-__device__ void trmm_inplace_right(const X *A, int lda, X *B, int ldb, int n) {
-    const int tid = threadIdx.x, bd = blockDim.x;
-    for (int i = 0; i < n; ++i) {
-        for (int j = i + tid; j < n; j += bd) {
-            X s = XOps<X>::zero();
-            for (int l = i; l <= j; ++l) s = s + A[i * lda + l] * B[l * ldb + j];
-            B[i * ldb + j] = s;
-        }
-        __syncthreads();
-    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
 // One-sided (Hestenes) Jacobi on the columns of B (nrow x ncol, column-major,
-// ld ldb): rotate column pairs until every pair is orthogonal to tol
-// (|b_p . b_q| <= tol |b_p| |b_q|).  Parallel ordering: round-robin
-// tournament, one warp per pair, all pairs of a round disjoint.  Optionally
-// accumulates the rotations into V (ncol x ncol, column-major, ld ldv).
-// Bounded by max_sweeps.  Returns sweeps run.
+// ld ldb) with the rotations accumulated into V (ncol x ncol, ld ldv; V must
+// hold I on entry).  Round-robin tournament ordering; each half-warp rotates
+// one column pair, so a round is ceil(ncol/2) disjoint pairs and one
+// barrier.  Squared column norms are kept in alpha and updated
+// analytically after each rotation (alpha_p - t g, alpha_q + t g), then
+// recomputed exactly at every sweep; only b_p . b_q is reduced per pair.
+// A pair is rotated while g^2 > tol^2 alpha_p alpha_q.  Bounded by
+// max_sweeps.  On return alpha holds exact squared norms.
 // ---------------------------------------------------------------------------
-template <typename J>
-__device__ int jacobi_cols(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J tol, int max_sweeps,
+template <typename J, int MAXE>
+__device__ int jacobi_hw_n(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *alpha, J tol, int max_sweeps,
                            int *s_flag) {
-    const int N = ncol + (ncol & 1);
-    const int npairs = N / 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // MAXE elements per lane: nrow, ncol <= 16 * MAXE
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int lane = tid & 31, half = lane >> 4, l16 = lane & 15, warp = tid >> 5, nw = bd >> 5;
+    const int N = ncol + (ncol & 1), npairs = N / 2, M = N - 1;
+    const J tol2 = tol * tol;
     int sweep = 0;
-    if (ncol < 2) return 0;
-    for (; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) *s_flag = 0;
+    for (;; ++sweep) {
+        for (int c = tid; c < ncol; c += bd) {
+            J s = 0;
+            for (int i = 0; i < nrow; ++i) s = fma(B[(size_t)c * ldb + i], B[(size_t)c * ldb + i], s);
+            alpha[c] = s;
+        }
+        if (tid == 0) *s_flag = 0;
         __syncthreads();
-        for (int rnd = 0; rnd < N - 1; ++rnd) {
-            for (int pr = warp; pr < npairs; pr += nw) {
-                int p, q;
-                if (pr == 0) {
-                    p = N - 1;
-                    q = rnd;
-                } else {
-                    p = (rnd + pr) % (N - 1);
-                    q = (rnd - pr + N - 1) % (N - 1);
-                }
-                if (p >= ncol || q >= ncol) continue;
-                if (p > q) { int tmp = p; p = q; q = tmp; }
-                J *bp = B + (size_t)p * ldb, *bq = B + (size_t)q * ldb;
-                J a = 0, b = 0, c = 0;
-                for (int i = lane; i < nrow; i += 32) {
-                    J x = bp[i], y = bq[i];
-                    a = fma(x, x, a);
-                    b = fma(y, y, b);
-                    c = fma(x, y, c);
-                }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                c = warp_sum(c);
-                if (a > (J)0 && b > (J)0 && fabs(c) > tol * sqrt(a) * sqrt(b)) {
-                    J zeta = (b - a) / (c + c);
-                    J t;
-                    if (fabs(zeta) > (J)1e15)
-                        t = (J)0.5 / zeta;
-                    else
-                        t = (zeta >= (J)0 ? (J)1 : (J)-1) / (fabs(zeta) + sqrt((J)1 + zeta * zeta));
-                    J cs = (J)1 / sqrt((J)1 + t * t), sn = cs * t;
-                    for (int i = lane; i < nrow; i += 32) {
-                        J x = bp[i], y = bq[i];
-                        bp[i] = cs * x - sn * y;
-                        bq[i] = sn * x + cs * y;
+        if (sweep >= max_sweeps || ncol < 2) break;
+        for (int rnd = 0; rnd < M; ++rnd) {
+            for (int base = 2 * warp; base < npairs; base += 2 * nw) {
+                const int pr = base + half;
+                int p = 0, q = 0;
+                bool valid = pr < npairs;
+                if (valid) {
+                    if (pr == 0) {
+                        p = M;
+                        q = rnd;
+                    } else {
+                        p = rnd + pr;
+                        if (p >= M) p -= M;
+                        q = rnd - pr + M;
+                        if (q >= M) q -= M;
                     }
-                    if (V) {
-                        J *vp = V + (size_t)p * ldv, *vq = V + (size_t)q * ldv;
-                        for (int i = lane; i < ncol; i += 32) {
-                            J x = vp[i], y = vq[i];
-                            vp[i] = cs * x - sn * y;
-                            vq[i] = sn * x + cs * y;
+                    if (p >= ncol || q >= ncol) valid = false;
+                    if (p > q) { int tmp = p; p = q; q = tmp; }
+                }
+                J *bp = B + (size_t)p * ldb, *bq = B + (size_t)q * ldb;
+                J *vp = V + (size_t)p * ldv, *vq = V + (size_t)q * ldv;
+                J x[MAXE], y[MAXE], vx[MAXE], vy[MAXE];
+                J g = 0;
+#pragma unroll
+                for (int e = 0; e < MAXE; ++e) {
+                    const int i = l16 + 16 * e;
+                    const bool in = valid && i < nrow;
+                    x[e] = in ? bp[i] : (J)0;
+                    y[e] = in ? bq[i] : (J)0;
+                    g = fma(x[e], y[e], g);
+                }
+#pragma unroll
+                for (int e = 0; e < MAXE; ++e) {
+                    const int i = l16 + 16 * e;
+                    const bool in = valid && i < ncol;
+                    vx[e] = in ? vp[i] : (J)0;
+                    vy[e] = in ? vq[i] : (J)0;
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, 16);
+                if (valid) {
+                    const J a = alpha[p], b = alpha[q];
+                    if (a > (J)0 && b > (J)0 && g * g > tol2 * a * b) {
+                        const J zeta = j_div(b - a, g + g);
+                        const J az = fabs(zeta);
+                        J t;
+                        if (az > (J)1e15) {
+                            t = j_div((J)0.5, zeta);
+                        } else {
+                            const J w = (J)1 + zeta * zeta;
+                            t = j_div((J)1, az + w * j_rsqrt(w));
+                            if (zeta < (J)0) t = -t;
+                        }
+                        const J cs = j_rsqrt((J)1 + t * t), sn = cs * t;
+#pragma unroll
+                        for (int e = 0; e < MAXE; ++e) {
+                            const int i = l16 + 16 * e;
+                            if (i < nrow) {
+                                bp[i] = cs * x[e] - sn * y[e];
+                                bq[i] = sn * x[e] + cs * y[e];
+                            }
+                            if (i < ncol) {
+                                vp[i] = cs * vx[e] - sn * vy[e];
+                                vq[i] = sn * vx[e] + cs * vy[e];
+                            }
+                        }
+                        if (l16 == 0) {
+                            alpha[p] = a - t * g;
+                            alpha[q] = b + t * g;
+                            *s_flag = 1;
                         }
                     }
-                    if (lane == 0) *s_flag = 1;
                 }
             }
             __syncthreads();
@@ -189,6 +238,13 @@ __device__ int jacobi_cols(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J t
         if (!rotated) break;
     }
     return sweep;
+}
+
+template <typename J>
+__device__ int jacobi_hw(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *alpha, J tol, int max_sweeps,
+                         int *s_flag) {
+    if (nrow <= 64 && ncol <= 64) return jacobi_hw_n<J, 4>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
+    return jacobi_hw_n<J, 10>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
 }
 
 // rank of each of n keys in descending order (ties by index) -> order[rank] = i
@@ -205,6 +261,64 @@ __device__ void sort_desc(const K *key, int n, int *order) {
     }
     __syncthreads();
 }
+
+// Largest singular value of B (nrow x k, column-major, ld): 16 steps of
+// power iteration on B^T B started from its row with the largest diagonal,
+// bounded below by |B|_F / sqrt(k).  One warp does the iteration.
+template <typename J>
+__device__ double top_singular_value(const J *B, int ld, int nrow, int k, J *BtB, J *x, J *y) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e % k;
+        J s = 0;
+        for (int p = 0; p < nrow; ++p) s = fma(B[(size_t)i * ld + p], B[(size_t)j * ld + p], s);
+        BtB[i * k + j] = s;
+    }
+    __syncthreads();
+    double result = 0.0;
+    if (tid < 32) {
+        J fro = 0, dmax = -1;
+        int imax = 0;
+        for (int i = tid; i < k; i += 32) {
+            const J d = BtB[i * k + i];
+            fro += d;
+            if (d > dmax) { dmax = d; imax = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            fro += __shfl_xor_sync(0xffffffffu, fro, o);
+            const J od = __shfl_xor_sync(0xffffffffu, dmax, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, imax, o);
+            if (od > dmax || (od == dmax && oi < imax)) { dmax = od; imax = oi; }
+        }
+        for (int i = tid; i < k; i += 32) x[i] = BtB[imax * k + i];
+        __syncwarp();
+        J lam = 0;
+        for (int it = 0; it < 16; ++it) {
+            J nrm = 0, xx = 0;
+            for (int i = tid; i < k; i += 32) {
+                J s = 0;
+                for (int j = 0; j < k; ++j) s = fma(BtB[i * k + j], x[j], s);
+                y[i] = s;
+                nrm = fma(s, s, nrm);
+                xx = fma(x[i], x[i], xx);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+                xx += __shfl_xor_sync(0xffffffffu, xx, o);
+            }
+            __syncwarp();
+            lam = xx > (J)0 ? sqrt(nrm / xx) : (J)0;       // |B^T B x| / |x|
+            const J inv = nrm > (J)0 ? j_rsqrt(nrm) : (J)0;
+            for (int i = tid; i < k; i += 32) x[i] = y[i] * inv;
+            __syncwarp();
+        }
+        const J lower = k > 0 ? fro / (J)k : (J)0;
+        result = sqrt((double)(lam > lower ? lam : lower));
+    }
+    return result;   // valid in threads 0..31
+}
+
+__host__ __device__ inline size_t al16x(size_t b) { return (b + 15) / 16 * 16; }
 
 // bump allocator over dynamic shared memory
 struct Carve {
@@ -257,10 +371,12 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_chol(SmallArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Carve cv{smem_raw};
     X *W = cv.take<X>((size_t)ld * ld);
+    X *R = cv.take<X>((size_t)ld * ld);
+    X *Mw = cv.take<X>((size_t)ld * ld);
     X *M = cv.take<X>((size_t)ld * ld);
-    X *Q = cv.take<X>((size_t)ld * ld);
     __shared__ double red[32];
-    __shared__ X s_piv;
+    __shared__ X piv3[3];
+    X *dinv = cv.take<X>(ld);
     const int tid = threadIdx.x, bd = blockDim.x;
     const double *P2 = a.PG;
     const double *G = a.PG + (int64_t)a.rmax * a.cmax;
@@ -286,24 +402,24 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_chol(SmallArgs a) {
         W[i * ld + j] = XOps<X>::from(i <= j ? G[i * ld + j] : 0.0);
     }
     __syncthreads();
-    chol_drop<X>(W, ld, g, thr, &s_piv);
-    tri_inv<X>(W, ld, g, M, ld);
+    chol_drop<X>(W, ld, g, thr, R, ld, piv3);
+    tri_inv<X>(R, ld, g, Mw, ld, M, ld, dinv);
     // round M1 to the storage type: that is the matrix the QR2 pass applies
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
-        double v = round_to(a.dtype, XOps<X>::to(M[i * ld + j]));
+        const double v = round_to(a.dtype, XOps<X>::to(M[i * ld + j]));
         a.M1[i * ld + j] = v;
         M[i * ld + j] = XOps<X>::from(v);
     }
     __syncthreads();
-    tri_inv<X>(M, ld, g, Q, ld);
+    tri_inv<X>(M, ld, g, Mw, ld, W, ld, dinv);
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
-        a.R1p[i * ld + j] = XOps<X>::to(Q[i * ld + j]);
+        a.R1p[i * ld + j] = XOps<X>::to(W[i * ld + j]);
     }
 }
 
-size_t small_chol_smem(int cmax) { return 3 * (size_t)cmax * cmax * 8 + 64; }
+size_t small_chol_smem(int cmax) { return 4 * al16x((size_t)cmax * cmax * 8) + al16x((size_t)cmax * 8) + 64; }
 
 pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s) {
     const size_t smem = small_chol_smem(a.cmax);
@@ -322,26 +438,36 @@ pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Second CholeskyQR pass, the core E and its SVD, truncation, convergence,
 // and the update coefficients.
+//
+// The SVD of E runs one-sided Jacobi on the rows of E (the columns of E^T),
+// accumulating the rotations: E^T V = W Sigma, so V holds U_E.  (On E's
+// columns the same matrices needed about 40% more sweeps.)  FP64 path: all
+// in FP64, U_E = V, sigma = column norms.  FP32 path: sweeps in FP32, then
+// the top-r columns of V are re-orthonormalised by a double-float
+// CholeskyQR (leading spans kept) and sigma_i = |E^T q_i| in double-float:
+// a Rayleigh quotient, second-order accurate in the FP32 rotation error.
 // ---------------------------------------------------------------------------
 struct CoreLayout {
-    size_t phaseA;   // 4 g x g X matrices
-    size_t phaseB;   // Jacobi: B and V (J), keys, order
+    size_t keep;     // E, Rinv, Ptot as X (persist across phases)
+    size_t phaseA;   // 6 g x g X matrices
+    size_t phaseB;   // Jacobi: B and V (J), alpha (J), order (int)
     size_t phaseC;   // finish
     size_t total;
 };
 
-__host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
-
 __host__ __device__ inline CoreLayout core_layout(int rmax, int cmax, int jsize) {
     CoreLayout L;
     const int nmax = rmax + cmax;
-    L.phaseA = 4 * al16((size_t)cmax * cmax * 8);
-    L.phaseB = 2 * al16((size_t)nmax * nmax * jsize) + al16((size_t)nmax * 8) + al16((size_t)nmax * 4);
-    // Vh, Bd, UE: nmax x rmax X; Gb, Mb: rmax x rmax X; Bsin: nmax x rmax J; sig: rmax X
-    L.phaseC = 3 * al16((size_t)nmax * rmax * 8) + 2 * al16((size_t)rmax * rmax * 8) +
-               al16((size_t)nmax * rmax * jsize) + al16((size_t)rmax * 8) + al16((size_t)rmax * 4);
+    L.keep = al16x((size_t)nmax * nmax * 8) + al16x((size_t)cmax * cmax * 8) + al16x((size_t)rmax * cmax * 8);
+    L.phaseA = 5 * al16x((size_t)cmax * cmax * 8);
+    L.phaseB = 2 * al16x((size_t)nmax * nmax * jsize) + al16x((size_t)nmax * jsize) + al16x((size_t)nmax * 4);
+    // Vr, Q, Yt: nmax x rmax X; Gb, Rb, Mw, Mb: rmax x rmax X; Bs: nmax x rmax J;
+    // BtB: rmax^2 J; xv, yv: rmax J; sig: rmax X; ord2: rmax int
+    L.phaseC = 3 * al16x((size_t)nmax * rmax * 8) + 4 * al16x((size_t)rmax * rmax * 8) +
+               al16x((size_t)nmax * rmax * jsize) + al16x((size_t)rmax * rmax * jsize) + 2 * al16x((size_t)rmax * jsize) +
+               al16x((size_t)rmax * 8) + al16x((size_t)rmax * 4);
     const size_t bc = L.phaseB + L.phaseC;
-    L.total = (L.phaseA > bc ? L.phaseA : bc) + 64;
+    L.total = L.keep + (L.phaseA > bc ? L.phaseA : bc) + 64;
     return L;
 }
 
@@ -354,26 +480,36 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
     DevState *st = a.st;
     if (st->done) return;
     const int r = st->r_cur, g = st->g, nc = r + g, t = st->t;
-    const int ld = a.cmax, nmax = a.rmax + a.cmax, lde = nmax;
+    const int ld = a.cmax, nmax = a.rmax + a.cmax;
     const int tid = threadIdx.x, bd = blockDim.x;
-    const CoreLayout CL = core_layout(a.rmax, a.cmax, (int)sizeof(J));
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ X s_piv;
     __shared__ int s_flag;
     __shared__ double red[32];
     __shared__ int s_rnew;
     __shared__ double s_measure, s_sin, s_cos;
     __shared__ int s_bad;
+    __shared__ X piv3[3];
+    __shared__ X dinv[256];
     const double u = unit_roundoff(a.dtype);
+    long long clk[6];
+    clk[0] = clock64();
     if (tid == 0) s_bad = 0;
+    const CoreLayout CL = core_layout(a.rmax, a.cmax, (int)sizeof(J));
+    Carve keep{smem_raw};
+    X *Ex = keep.take<X>((size_t)nmax * nmax);    // E, column-major, ld nc
+    X *Rinv = keep.take<X>((size_t)ld * ld);      // g x g, ld cmax
+    X *Ptx = keep.take<X>((size_t)a.rmax * ld);   // r x g, ld cmax
+    unsigned char *work = smem_raw + CL.keep;
 
-    // ---- phase A: R2 = chol(G2), M2 = R2^{-1}, R = R2 R1p, Rinv = M1 M2
+    // ---- phase A: R2 = chol(G2), M2 = R2^{-1}, R = R2 R1p, Rinv = M1 M2, E
     {
-        Carve cv{smem_raw};
+        Carve cv{work};
         X *W = cv.take<X>((size_t)ld * ld);
+        X *R2 = cv.take<X>((size_t)ld * ld);
         X *M2 = cv.take<X>((size_t)ld * ld);
-        X *Rr = cv.take<X>((size_t)ld * ld);
-        X *Mi = cv.take<X>((size_t)ld * ld);
+        X *R1 = cv.take<X>((size_t)ld * ld);
+        X *M1 = cv.take<X>((size_t)ld * ld);
+        X *Rr = W;   // W is free once M2 is formed
         double dmax = 0.0;
         for (int j = tid; j < g; j += bd) dmax = a.G2[j * ld + j] > dmax ? a.G2[j * ld + j] : dmax;
         dmax = block_max<double>(dmax, red);
@@ -382,147 +518,141 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
         for (int e = tid; e < g * g; e += bd) {
             const int i = e / g, j = e % g;
             W[i * ld + j] = XOps<X>::from(i <= j ? a.G2[i * ld + j] : 0.0);
-            Rr[i * ld + j] = XOps<X>::from(a.R1p[i * ld + j]);
-            Mi[i * ld + j] = XOps<X>::from(a.M1[i * ld + j]);
+            R1[i * ld + j] = XOps<X>::from(a.R1p[i * ld + j]);
+            M1[i * ld + j] = XOps<X>::from(a.M1[i * ld + j]);
+        }
+        for (int e = tid; e < r * g; e += bd) {
+            const int l = e / g, j = e % g;
+            Ptx[l * ld + j] = XOps<X>::from(a.Ptot[l * ld + j]);
         }
         __syncthreads();
-        chol_drop<X>(W, ld, g, thr, &s_piv);
-        tri_inv<X>(W, ld, g, M2, ld);
-        trmm_inplace_right<X>(W, ld, Rr, ld, g);     // Rr <- R2 R1p
-        trmm_inplace_left<X>(Mi, ld, M2, ld, g);     // Mi <- M1 M2
-        // E (column-major, ld lde) and Rinv (kept in Ym's scratch: the E buffer tail)
-        double *Rinv = a.E + (size_t)lde * lde;
+        chol_drop<X>(W, ld, g, thr, R2, ld, piv3);
+        tri_inv<X>(R2, ld, g, W, ld, M2, ld, dinv);
+        trmm_upper<X>(R2, ld, R1, ld, g, Rr, ld);     // R = R2 R1p
+        trmm_upper<X>(M1, ld, M2, ld, g, Rinv, ld);   // Rinv = M1 M2
         for (int e = tid; e < nc * nc; e += bd) {
             const int q = e / nc, p = e % nc;   // column q, row p
-            double v = 0.0;
+            X v = XOps<X>::zero();
             if (p < r) {
-                if (q < r) v = (p == q) ? a.sigma[p] : 0.0;
-                else v = a.Ptot[p * ld + (q - r)];
+                if (q < r) v = (p == q) ? XOps<X>::from(a.sigma[p]) : XOps<X>::zero();
+                else v = Ptx[p * ld + (q - r)];
             } else if (q >= r) {
-                v = XOps<X>::to(Rr[(p - r) * ld + (q - r)]);
+                v = Rr[(p - r) * ld + (q - r)];
             }
-            if (!isfinite(v)) s_bad = 1;
-            a.E[(size_t)q * lde + p] = v;
-        }
-        for (int e = tid; e < g * g; e += bd) {
-            const int i = e / g, j = e % g;
-            Rinv[i * ld + j] = XOps<X>::to(Mi[i * ld + j]);
+            if (!isfinite(x_hi(v))) s_bad = 1;
+            Ex[q * nc + p] = v;
         }
         __syncthreads();
     }
 
-    // ---- phase B: Jacobi on the columns of E
-    Carve cv{smem_raw};
+    // ---- phase B: Jacobi on the rows of E: B = E^T (column p = row p of E)
+    Carve cv{work};
     J *B = cv.take<J>((size_t)nmax * nmax);
     J *V = cv.take<J>((size_t)nmax * nmax);
-    double *key = cv.take<double>(nmax);
+    J *alpha = cv.take<J>(nmax);
     int *order = cv.take<int>(nmax);
-    X *Vh = cv.take<X>((size_t)nmax * a.rmax);
-    X *Bd = cv.take<X>((size_t)nmax * a.rmax);
-    X *UE = cv.take<X>((size_t)nmax * a.rmax);
+    X *Vr = cv.take<X>((size_t)nmax * a.rmax);
+    X *Q = cv.take<X>((size_t)nmax * a.rmax);
+    X *Yt = cv.take<X>((size_t)nmax * a.rmax);
     X *Gb = cv.take<X>((size_t)a.rmax * a.rmax);
+    X *Rb = cv.take<X>((size_t)a.rmax * a.rmax);
+    X *Mw = cv.take<X>((size_t)a.rmax * a.rmax);
     X *Mb = cv.take<X>((size_t)a.rmax * a.rmax);
     J *Bs = cv.take<J>((size_t)nmax * a.rmax);
+    J *BtB = cv.take<J>((size_t)a.rmax * a.rmax);
+    J *xv = cv.take<J>(a.rmax);
+    J *yv = cv.take<J>(a.rmax);
     X *sig = cv.take<X>(a.rmax);
     int *ord2 = cv.take<int>(a.rmax);
-    const bool with_v = sizeof(J) == 4;
+    const bool f32 = sizeof(J) == 4;
     for (int e = tid; e < nc * nc; e += bd) {
-        const int q = e / nc, p = e % nc;
-        B[q * nc + p] = (J)a.E[(size_t)q * lde + p];
-        if (with_v) V[q * nc + p] = (p == q) ? (J)1 : (J)0;
+        const int col = e / nc, i = e % nc;   // B column col = row col of E; entry i = E[col][i]
+        B[col * nc + i] = (J)x_hi(Ex[i * nc + col]) + (J)(f32 ? 0.f : (float)0);
+        if (!f32) B[col * nc + i] = (J)XOps<X>::to(Ex[i * nc + col]);
+        V[col * nc + i] = (i == col) ? (J)1 : (J)0;
     }
     __syncthreads();
-    const J eps_j = sizeof(J) == 4 ? (J)1.1920928955078125e-07 : (J)2.220446049250313e-16;
+    const J eps_j = f32 ? (J)1.1920928955078125e-07 : (J)2.220446049250313e-16;
     const J tol = (J)2 * sqrt((J)nc) * eps_j;
-    jacobi_cols<J>(B, nc, nc, nc, with_v ? V : nullptr, nc, tol, sizeof(J) == 4 ? 20 : 30, &s_flag);
-    for (int i = tid; i < nc; i += bd) {
-        double s = 0.0;
-        for (int p = 0; p < nc; ++p) s += (double)B[i * nc + p] * (double)B[i * nc + p];
-        key[i] = s;
-    }
-    __syncthreads();
-    sort_desc<double>(key, nc, order);
+    clk[1] = clock64();
+    const int nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, f32 ? 20 : 30, &s_flag);
+    clk[2] = clock64();
+    sort_desc<J>(alpha, nc, order);
     const int rsel = a.r < nc ? a.r : nc;
 
-    // ---- phase C: top-r left vectors and singular values
-    if (with_v) {
-        // v_s = normalised V[:, order[s]] (X); b_s = E v_s; sigma_s = |b_s|
-        for (int s = tid >> 5; s < rsel; s += bd >> 5) {
-            const int col = order[s];
-            X nrm = XOps<X>::zero();
-            for (int i = (tid & 31); i < nc; i += 32) {
-                X v = XOps<X>::from((double)V[col * nc + i]);
-                nrm = nrm + v * v;
-            }
-            // warp sum in X via shuffles of the two halves
-            for (int o = 16; o > 0; o >>= 1) nrm = nrm + x_shfl_xor(nrm, o);
-            nrm = XOps<X>::sqrt_(nrm);
-            for (int i = (tid & 31); i < nc; i += 32)
-                Vh[s * nc + i] = XOps<X>::from((double)V[col * nc + i]) / nrm;
+    // ---- phase C: top-r left vectors of E and singular values
+    if (f32) {
+        // The rotated rows b_s = E^T v_s = sigma_s w_s give the left vectors
+        // u_s = E b_s / sigma_s^2 (a power step that damps the FP32 rotation
+        // error of direction j by sigma_j / sigma_s).  Vr_s = E b_s in
+        // double-float, orthonormalised by CholeskyQR (leading spans kept);
+        // then sigma_s = |E^T q_s| (Rayleigh quotient).
+        for (int e = tid; e < nc * rsel; e += bd) {
+            const int s = e / nc, p = e % nc;
+            const J *bs = B + (size_t)order[s] * nc;
+            X acc = XOps<X>::zero();
+            for (int j = 0; j < nc; ++j) acc = acc + Ex[j * nc + p] * XOps<X>::from_f((float)bs[j]);
+            Vr[s * nc + p] = acc;
         }
         __syncthreads();
+        for (int e = tid; e < rsel * rsel; e += bd) {
+            const int i = e / rsel, j = e % rsel;
+            X acc = XOps<X>::zero();
+            if (i <= j)
+                for (int p = 0; p < nc; ++p) acc = acc + Vr[i * nc + p] * Vr[j * nc + p];
+            Gb[i * a.rmax + j] = acc;
+        }
+        __syncthreads();
+        chol_drop<X>(Gb, a.rmax, rsel, XOps<X>::from(1e-60), Rb, a.rmax, piv3);
+        tri_inv<X>(Rb, a.rmax, rsel, Mw, a.rmax, Mb, a.rmax, dinv);
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
             X acc = XOps<X>::zero();
-            for (int q = 0; q < nc; ++q) acc = acc + XOps<X>::from(a.E[(size_t)q * lde + p]) * Vh[s * nc + q];
-            Bd[s * nc + p] = acc;
+            for (int l = 0; l <= s; ++l) acc = acc + Vr[l * nc + p] * Mb[l * a.rmax + s];
+            Q[s * nc + p] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < nc * rsel; e += bd) {
+            const int s = e / nc, j = e % nc;
+            X acc = XOps<X>::zero();
+            for (int p = 0; p < nc; ++p) acc = acc + Ex[j * nc + p] * Q[s * nc + p];
+            Yt[s * nc + j] = acc;
         }
         __syncthreads();
         for (int s = tid; s < rsel; s += bd) {
             X acc = XOps<X>::zero();
-            for (int p = 0; p < nc; ++p) acc = acc + Bd[s * nc + p] * Bd[s * nc + p];
+            for (int j = 0; j < nc; ++j) acc = acc + Yt[s * nc + j] * Yt[s * nc + j];
             sig[s] = XOps<X>::sqrt_(acc);
         }
         __syncthreads();
         sort_desc<X>(sig, rsel, ord2);
-        // Gram of the re-ordered columns, CholeskyQR
-        for (int e = tid; e < rsel * rsel; e += bd) {
-            const int i = e / rsel, j = e % rsel;
-            X acc = XOps<X>::zero();
-            if (i <= j) {
-                const X *bi = Bd + ord2[i] * nc, *bj = Bd + ord2[j] * nc;
-                for (int p = 0; p < nc; ++p) acc = acc + bi[p] * bj[p];
-            }
-            Gb[i * a.rmax + j] = acc;
-        }
-        __syncthreads();
-        {
-            const double s0 = XOps<X>::to(sig[ord2[0]]);
-            const double e2 = (nc * u) * (nc * u) * s0 * s0;
-            chol_drop<X>(Gb, a.rmax, rsel, XOps<X>::from(e2), &s_piv);
-        }
-        tri_inv<X>(Gb, a.rmax, rsel, Mb, a.rmax);
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
-            X acc = XOps<X>::zero();
-            for (int l = 0; l <= s; ++l) acc = acc + Bd[ord2[l] * nc + p] * Mb[l * a.rmax + s];
-            UE[s * nc + p] = acc;
+            Vr[s * nc + p] = Q[ord2[s] * nc + p];
         }
+        for (int s = tid; s < rsel; s += bd) Yt[s] = sig[ord2[s]];
         __syncthreads();
-        // singular values in the new order (reuse Vh's first column as scratch)
-        for (int s = tid; s < rsel; s += bd) Vh[s] = sig[ord2[s]];
-        __syncthreads();
-        for (int s = tid; s < rsel; s += bd) sig[s] = Vh[s];
+        for (int e = tid; e < nc * rsel; e += bd) Q[e] = Vr[e];
+        for (int s = tid; s < rsel; s += bd) sig[s] = Yt[s];
         __syncthreads();
     } else {
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
-            const double nrm = sqrt(key[order[s]]);
-            UE[s * nc + p] = XOps<X>::from(nrm > 0.0 ? (double)B[order[s] * nc + p] / nrm : 0.0);
+            Q[s * nc + p] = XOps<X>::from((double)V[order[s] * nc + p]);
         }
-        for (int s = tid; s < rsel; s += bd) sig[s] = XOps<X>::from(sqrt(key[order[s]]));
+        for (int s = tid; s < rsel; s += bd) sig[s] = XOps<X>::from(sqrt((double)alpha[order[s]]));
         __syncthreads();
     }
-
+    clk[3] = clock64();
     // truncation: keep min(r, #sigma > nc u sigma_1)
     if (tid == 0) {
         const double s0 = XOps<X>::to(sig[0]);
         const double thr = nc * u * s0;
-        int keep = 0;
+        int keepn = 0;
         for (int s = 0; s < rsel; ++s)
-            if (XOps<X>::to(sig[s]) > thr) ++keep;
-        if (!(s0 == s0) || !isfinite(s0)) s_bad = 1;
-        s_rnew = keep;
+            if (XOps<X>::to(sig[s]) > thr) ++keepn;
+        if (!isfinite(s0)) s_bad = 1;
+        s_rnew = keepn;
         s_measure = 1.0;
         s_sin = 1.0;
         s_cos = 0.0;
@@ -538,26 +668,18 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
         if (a.criterion == POD_SUBSPACE) {
             for (int e = tid; e < nr * k; e += bd) {
                 const int cidx = e / nr, p = e % nr;
-                Bs[cidx * nr + p] = (J)XOps<X>::to(UE[cidx * nc + k + p]);
+                Bs[cidx * nr + p] = (J)XOps<X>::to(Q[cidx * nc + k + p]);
             }
             __syncthreads();
-            jacobi_cols<J>(Bs, nr, nr, k, nullptr, 0, (J)2 * sqrt((J)(nr > 1 ? nr : 1)) * eps_j,
-                           sizeof(J) == 4 ? 20 : 30, &s_flag);
-            double mx = 0.0;
-            for (int cidx = tid; cidx < k; cidx += bd) {
-                double s = 0.0;
-                for (int p = 0; p < nr; ++p) s += (double)Bs[cidx * nr + p] * (double)Bs[cidx * nr + p];
-                mx = s > mx ? s : mx;
-            }
-            mx = block_max<double>(mx, red);
+            const double smax = top_singular_value<J>(Bs, nr, nr, k, BtB, xv, yv);
             if (tid == 0) {
-                s_sin = sqrt(mx);
-                s_measure = s_sin;
+                s_sin = smax;
+                s_measure = smax;
             }
         } else {
             double mn = 1e300;
             for (int i = tid; i < k; i += bd) {
-                double c = fabs(XOps<X>::to(UE[i * nc + i]));
+                double c = fabs(XOps<X>::to(Q[i * nc + i]));
                 mn = c < mn ? c : mn;
             }
             mn = -block_max<double>(-mn, red);
@@ -568,29 +690,26 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
         }
         __syncthreads();
     }
-
+    clk[4] = clock64();
     // Y = Rinv U_E[r:, :rn] (g x rn), X = U_E[:r, :rn] - Ptot Y (r x rn)
-    {
-        const double *Rinv = a.E + (size_t)lde * lde;
-        for (int e = tid; e < g * rn; e += bd) {
-            const int j = e / rn, q = e % rn;
-            X acc = XOps<X>::zero();
-            for (int l = j; l < g; ++l) acc = acc + XOps<X>::from(Rinv[j * ld + l]) * UE[q * nc + r + l];
-            Bd[j * a.rmax + q] = acc;   // Bd reused as Y (g x rn, ld rmax)
-        }
-        __syncthreads();
-        for (int e = tid; e < g * rn; e += bd) {
-            const int j = e / rn, q = e % rn;
-            a.Ym[j * a.rmax + q] = XOps<X>::to(Bd[j * a.rmax + q]);
-        }
-        for (int e = tid; e < r * rn; e += bd) {
-            const int l = e / rn, q = e % rn;
-            X acc = UE[q * nc + l];
-            for (int j = 0; j < g; ++j) acc = acc - XOps<X>::from(a.Ptot[l * ld + j]) * Bd[j * a.rmax + q];
-            a.Xm[l * a.rmax + q] = XOps<X>::to(acc);
-        }
-        for (int s = tid; s < rn; s += bd) a.sigma[s] = XOps<X>::to(sig[s]);
+    for (int e = tid; e < g * rn; e += bd) {
+        const int j = e / rn, q = e % rn;
+        X acc = XOps<X>::zero();
+        for (int l = j; l < g; ++l) acc = acc + Rinv[j * ld + l] * Q[q * nc + r + l];
+        Yt[j * a.rmax + q] = acc;
     }
+    __syncthreads();
+    for (int e = tid; e < g * rn; e += bd) {
+        const int j = e / rn, q = e % rn;
+        a.Ym[j * a.rmax + q] = XOps<X>::to(Yt[j * a.rmax + q]);
+    }
+    for (int e = tid; e < r * rn; e += bd) {
+        const int l = e / rn, q = e % rn;
+        X acc = Q[q * nc + l];
+        for (int j = 0; j < g; ++j) acc = acc - Ptx[l * ld + j] * Yt[j * a.rmax + q];
+        a.Xm[l * a.rmax + q] = XOps<X>::to(acc);
+    }
+    for (int s = tid; s < rn; s += bd) a.sigma[s] = XOps<X>::to(sig[s]);
     __syncthreads();
     if (tid == 0) {
         st->r_new = rn;
@@ -609,13 +728,18 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
             dn = 1;
         }
         st->done_next = dn;
+        st->sweeps = nsweeps;
+        clk[5] = clock64();
+        for (int i = 0; i < 5; ++i) st->core_cycles[i] = clk[i + 1] - clk[i];
+        st->core_cycles[5] = clk[5] - clk[0];
     }
 }
 
 pod_status launch_core(const SmallArgs &a, cudaStream_t s) {
-    const size_t smem = core_smem_bytes(a.rmax, a.cmax, a.core_f64 ? POD_F64 : POD_F32);
+    const bool f64 = a.core_f64 || a.dtype == POD_F64;
+    const size_t smem = core_smem_bytes(a.rmax, a.cmax, f64 ? POD_F64 : POD_F32);
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
-    if (a.dtype == POD_F32 && !a.core_f64) {
+    if (!f64) {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_core<dfloat, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_core<dfloat, float><<<1, SMALL_THREADS, smem, s>>>(a);
     } else {
@@ -637,7 +761,6 @@ __global__ void k_finish(DevState *st) {
     if (st->done_next) st->done = 1;
 }
 
-pod_status launch_finish(DevState *st, cudaStream_t s);
 pod_status launch_finish(DevState *st, cudaStream_t s) {
     k_finish<<<1, 32, 0, s>>>(st);
     POD_CUDA_TRY(cudaGetLastError());
@@ -647,17 +770,20 @@ pod_status launch_finish(DevState *st, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Refinement (closing lines of Algorithm 1): with Y = A^T U (n x r),
 // CholeskyQR2 gives Y = Q R; SVD(R) = U_R S_R V_R^T by one-sided Jacobi in
-// FP64 with accumulated V_R; outputs sigma = S_R, VR (U <- U V_R) and
-// K = R^{-1} U_R (V <- Y K = Q U_R).  r <= 128, one CTA.
+// FP64 on the columns of R with accumulated V_R; outputs sigma = S_R,
+// VR (U <- U V_R) and K = R^{-1} U_R (V <- Y K = Q U_R).  One CTA.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SMALL_THREADS) k_refine_chol(RefineArgs a) {
     const int r = a.r;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Carve cv{smem_raw};
     double *W = cv.take<double>((size_t)r * r);
+    double *R = cv.take<double>((size_t)r * r);
+    double *Mw = cv.take<double>((size_t)r * r);
     double *M = cv.take<double>((size_t)r * r);
-    __shared__ double s_piv;
     __shared__ double red[32];
+    __shared__ double piv3[3];
+    __shared__ double dinv[256];
     const int tid = threadIdx.x, bd = blockDim.x;
     double dmax = 0.0;
     for (int j = tid; j < r; j += bd) dmax = a.G[j * r + j] > dmax ? a.G[j * r + j] : dmax;
@@ -668,11 +794,11 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_chol(RefineArgs a) {
     }
     __syncthreads();
     const double eps = r * 1.1102230246251565e-16;
-    chol_drop<double>(W, r, r, eps * eps * dmax, &s_piv);
-    tri_inv<double>(W, r, r, M, r);
+    chol_drop<double>(W, r, r, eps * eps * dmax, R, r, piv3);
+    tri_inv<double>(R, r, r, Mw, r, M, r, dinv);
     for (int e = tid; e < r * r; e += bd) {
         a.M1[e] = M[e];
-        a.R1p[e] = W[e];
+        a.R1p[e] = R[e];
     }
 }
 
@@ -680,16 +806,20 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
     const int r = a.r;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Carve cv{smem_raw};
-    double *W = cv.take<double>((size_t)r * r);   // R2 -> R (row-major upper)
+    double *W = cv.take<double>((size_t)r * r);
+    double *R2 = cv.take<double>((size_t)r * r);
     double *M2 = cv.take<double>((size_t)r * r);
-    double *B = cv.take<double>((size_t)r * r);   // column-major copy of R for Jacobi
-    double *V = cv.take<double>((size_t)r * r);
-    double *key = cv.take<double>(r);
-    int *order = cv.take<int>(r);
     double *R1 = cv.take<double>((size_t)r * r);
-    __shared__ double s_piv;
+    double *Rr = cv.take<double>((size_t)r * r);   // R = R2 R1
+    double *Mi = cv.take<double>((size_t)r * r);   // R^{-1} = M1 M2
+    double *B = cv.take<double>((size_t)r * r);
+    double *V = cv.take<double>((size_t)r * r);
+    double *alpha = cv.take<double>(r);
+    int *order = cv.take<int>(r);
     __shared__ int s_flag;
     __shared__ double red[32];
+    __shared__ double piv3[3];
+    __shared__ double dinv[256];
     const int tid = threadIdx.x, bd = blockDim.x;
     double dmax = 0.0;
     for (int j = tid; j < r; j += bd) dmax = a.G2[j * r + j] > dmax ? a.G2[j * r + j] : dmax;
@@ -698,49 +828,41 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
         const int i = e / r, j = e % r;
         W[e] = i <= j ? a.G2[i * r + j] : 0.0;
         R1[e] = a.R1p[e];
+        Mi[e] = a.M1[e];
     }
     __syncthreads();
     const double eps = r * 1.1102230246251565e-16;
-    chol_drop<double>(W, r, r, eps * eps * dmax, &s_piv);
-    tri_inv<double>(W, r, r, M2, r);
-    trmm_inplace_right<double>(W, r, R1, r, r);   // R1 <- R2 R1  (= R)
-    // Rinv = M1 M2 -> M2 (in place on the left factor copy)
-    double *Mi = W;   // reuse
-    for (int e = tid; e < r * r; e += bd) Mi[e] = a.M1[e];
-    __syncthreads();
-    trmm_inplace_left<double>(Mi, r, M2, r, r);   // Mi <- M1 M2 (= R^{-1})
+    chol_drop<double>(W, r, r, eps * eps * dmax, R2, r, piv3);
+    tri_inv<double>(R2, r, r, W, r, M2, r, dinv);
+    trmm_upper<double>(R2, r, R1, r, r, Rr, r);
+    trmm_upper<double>(Mi, r, M2, r, r, W, r);   // W <- R^{-1}
     for (int e = tid; e < r * r; e += bd) {
-        const int q = e / r, p = e % r;   // B column-major: column q
-        B[q * r + p] = R1[p * r + q];
+        const int q = e / r, p = e % r;   // B column-major: column q of R
+        B[q * r + p] = Rr[p * r + q];
         V[q * r + p] = (p == q) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_cols<double>(B, r, r, r, V, r, 2.0 * sqrt((double)r) * 2.220446049250313e-16, 40, &s_flag);
-    for (int i = tid; i < r; i += bd) {
-        double s = 0.0;
-        for (int p = 0; p < r; ++p) s += B[i * r + p] * B[i * r + p];
-        key[i] = s;
-    }
-    __syncthreads();
-    sort_desc<double>(key, r, order);
-    // sigma_s, V_R[:, s], U_R[:, s] = B[:, order[s]] / sigma_s, K = Rinv U_R
-    for (int s = tid; s < r; s += bd) a.sigma[s] = sqrt(key[order[s]]);
+    jacobi_hw<double>(B, r, r, r, V, r, alpha, 2.0 * sqrt((double)r) * 2.220446049250313e-16, 40, &s_flag);
+    sort_desc<double>(alpha, r, order);
+    // sigma_s, V_R[:, s], U_R[:, s] = B[:, order[s]] / sigma_s, K = R^{-1} U_R
+    for (int s = tid; s < r; s += bd) a.sigma[s] = sqrt(alpha[order[s]]);
     for (int e = tid; e < r * r; e += bd) {
         const int l = e / r, s = e % r;
         a.VR[l * r + s] = V[order[s] * r + l];
     }
     for (int e = tid; e < r * r; e += bd) {
         const int j = e / r, s = e % r;
-        const double sg = sqrt(key[order[s]]);
+        const double sg = sqrt(alpha[order[s]]);
         double acc = 0.0;
         if (sg > 0.0)
-            for (int l = j; l < r; ++l) acc += Mi[j * r + l] * B[order[s] * r + l] / sg;
+            for (int l = j; l < r; ++l) acc += W[j * r + l] * B[order[s] * r + l] / sg;
         a.K[j * r + s] = acc;
     }
 }
 
 pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s) {
-    const size_t smem = 2 * al16((size_t)a.r * a.r * 8) + 64;
+    const size_t smem = 4 * al16x((size_t)a.r * a.r * 8) + 64;
+    if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     POD_CUDA_TRY(cudaFuncSetAttribute(k_refine_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_refine_chol<<<1, SMALL_THREADS, smem, s>>>(a);
     POD_CUDA_TRY(cudaGetLastError());
@@ -748,7 +870,7 @@ pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s) {
 }
 
 pod_status launch_refine_svd(const RefineArgs &a, cudaStream_t s) {
-    const size_t smem = 5 * al16((size_t)a.r * a.r * 8) + al16((size_t)a.r * 8) + al16((size_t)a.r * 4) + 64;
+    const size_t smem = 8 * al16x((size_t)a.r * a.r * 8) + al16x((size_t)a.r * 8) + al16x((size_t)a.r * 4) + 64;
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     POD_CUDA_TRY(cudaFuncSetAttribute(k_refine_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_refine_svd<<<1, SMALL_THREADS, smem, s>>>(a);

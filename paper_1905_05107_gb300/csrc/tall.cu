@@ -6,21 +6,29 @@
 // plus Y = A^T U (closing refinement of Algorithm 1, ORT probabilities) and
 // the sign-reference dots.
 //
-// Every CTA walks row slabs of `bm` rows (grid-stride), stages the slab of U
-// and of the gathered columns of C in shared memory (row-major, so one row of
-// a slab is contiguous), and accumulates the small products with 4x4
-// register tiles.  FP32 data: the per-slab tile sums are FP32 and are flushed
-// into FP64 accumulators after every slab; the CTA's FP64 partial is written
-// to `part`, and a separate kernel sums the partials in a fixed order, so
-// results are bit-for-bit reproducible.
+// Each CTA walks row slabs of `bm` rows.  Slabs of U and of the gathered
+// columns A[:, idx[j]] are copied column-major into shared memory with
+// cp.async (16-byte copies when every column start is 16-byte aligned),
+// double-buffered so the next slab streams in while the current one is
+// used.  Every product is a 4x4 register tile fed by 128-bit shared loads:
+// the row-space products (C - U P, Z M1, U X + C Y) tile 4 rows x 4 output
+// columns, the Gram-type products (U^T C, Z^T Z) tile 4 x 4 outputs over
+// 4-row chunks.  FP32 tile sums are flushed into FP64 accumulators after
+// every slab.  The CTAs' FP64 partials are summed inside the kernel: the
+// last CTA to finish in each group of 16 sums its group, the last group sums
+// the groups, both in a fixed order (bit-reproducible), using atomic arrival
+// counters only (no waiting).
 #include "pod_internal.h"
 
 namespace {
 
+constexpr int TALL_THREADS = 256;
+constexpr int RED_GROUP = 16;
+
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
 template <typename T>
-__device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
+__device__ __forceinline__ void lds4(const T *p, T (&v)[4]) {
     if constexpr (sizeof(T) == 4) {
         float4 q = *reinterpret_cast<const float4 *>(p);
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
@@ -30,30 +38,76 @@ __device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
 }
-
-// Stage rows [i0, i0 + bm) of `ncols` columns into dst (row-major, ld),
-// zero-filling rows >= rows and columns ncols..round4(ncols)-1.
-template <typename T, typename ColFn>
-__device__ void load_slab(T *dst, int ld, int ncols, int bm, int rows, int64_t i0, ColFn col) {
-    const int nc4 = round4(ncols);
-    for (int e = threadIdx.x; e < nc4 * bm; e += blockDim.x) {
-        const int c = e / bm, i = e - c * bm;
-        T v = (T)0;
-        if (c < ncols && i < rows) v = col(c)[i0 + i];
-        dst[i * ld + c] = v;
+template <typename T>
+__device__ __forceinline__ void sts4(T *p, const T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
     }
 }
 
-// acc[p][q] += sum_{i < rows} X[i][p] Y[i][q] for p < na, q < nb (4x4 tiles;
-// tiles with ti > tj are skipped when sym).  acc is FP64 (ld ldacc), red is
-// scratch of blockDim.x * 16 T.  Ends with __syncthreads.
+// ---------------------------------------------------------------- cp.async
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem, int src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Copy rows [i0, i0 + bm) of `ncols` columns into dst (column-major, ld),
+// zero-filling rows at or beyond `mend`.  vec: 16-byte copies are legal.
+// `live(c)` false makes column c read as zeros (nothing is fetched).
+template <typename T, typename ColFn, typename LiveFn>
+__device__ __forceinline__ void issue_slab(T *dst, int ld, int ncols, int bm, int64_t i0, int64_t mend,
+                                           bool vec, ColFn col, LiveFn live) {
+    constexpr int V = 16 / sizeof(T);
+    if (vec) {
+        const int chunks = bm / V;
+        for (int e = threadIdx.x; e < ncols * chunks; e += blockDim.x) {
+            const int c = e / chunks, q = e - c * chunks;
+            const int64_t row = i0 + (int64_t)q * V;
+            const int64_t left = mend - row;
+            int bytes = left >= V ? 16 : (left > 0 ? (int)left * (int)sizeof(T) : 0);
+            if (!live(c)) bytes = 0;
+            const T *src = col(c) + (bytes > 0 ? row : 0);
+            cp_async16(dst + (size_t)c * ld + q * V, src, bytes);
+        }
+    } else {
+        for (int e = threadIdx.x; e < ncols * bm; e += blockDim.x) {
+            const int c = e / bm, q = e - c * bm;
+            const int64_t row = i0 + q;
+            const int bytes = (row < mend && live(c)) ? (int)sizeof(T) : 0;
+            const T *src = col(c) + (bytes > 0 ? row : 0);
+            cp_async_small<sizeof(T)>(dst + (size_t)c * ld + q, src, bytes);
+        }
+    }
+}
+
+struct AllLive {
+    __device__ bool operator()(int) const { return true; }
+};
+
+// ------------------------------------------------------------ micro-kernels
+// acc[p][q] += sum_i X[p][i] Y[q][i] over the bm rows of a slab (X, Y
+// column-major with leading dimension ld; p < na, q < nb).  Tiles of 4x4
+// outputs over 4-row chunks; tiles with ti > tj skipped when sym.  acc is
+// FP64 with leading dimension ldacc; red holds blockDim*16 T.  Ends with a
+// barrier.
 template <typename T>
-__device__ void acc_xty(const T *X, int ldx, int na, const T *Y, int ldy, int nb, int rows, bool sym,
-                        double *acc, int ldacc, T *red) {
-    const int bd = blockDim.x, tid = threadIdx.x;
-    const int ta = (na + 3) >> 2, tb = (nb + 3) >> 2;
-    const int nT = ta * tb;
-    if (nT == 0 || rows <= 0) return;
+__device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm, bool sym, double *acc,
+                         int ldacc, T *red) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int ta = (na + 3) >> 2, tb = (nb + 3) >> 2, nT = ta * tb;
+    const int chunks = bm >> 2;
+    if (nT == 0) return;
     if (nT * 2 > bd) {
         for (int tile = tid; tile < nT; tile += bd) {
             const int ti = tile / tb, tj = tile - ti * tb;
@@ -61,14 +115,18 @@ __device__ void acc_xty(const T *X, int ldx, int na, const T *Y, int ldy, int nb
             T a[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) a[e] = (T)0;
-            for (int i = 0; i < rows; ++i) {
-                T x[4], y[4];
-                ld4(X + i * ldx + 4 * ti, x);
-                ld4(Y + i * ldy + 4 * tj, y);
+            for (int rc = 0; rc < chunks; ++rc) {
+                T x[4][4], y[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) lds4(Y + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) a[u * 4 + v] = fma(x[u], y[v], a[u * 4 + v]);
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) a[u * 4 + v] = fma(x[u][w], y[v][w], a[u * 4 + v]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -85,14 +143,18 @@ __device__ void acc_xty(const T *X, int ldx, int na, const T *Y, int ldy, int nb
 #pragma unroll
     for (int e = 0; e < 16; ++e) a[e] = (T)0;
     if (grp < RG && !(sym && ti > tj)) {
-        for (int i = grp; i < rows; i += RG) {
-            T x[4], y[4];
-            ld4(X + i * ldx + 4 * ti, x);
-            ld4(Y + i * ldy + 4 * tj, y);
+        for (int rc = grp; rc < chunks; rc += RG) {
+            T x[4][4], y[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) lds4(Y + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) a[u * 4 + v] = fma(x[u], y[v], a[u * 4 + v]);
+                for (int v = 0; v < 4; ++v)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) a[u * 4 + v] = fma(x[u][w], y[v][w], a[u * 4 + v]);
         }
     }
     if (grp < RG) {
@@ -111,142 +173,280 @@ __device__ void acc_xty(const T *X, int ldx, int na, const T *Y, int ldy, int nb
     __syncthreads();
 }
 
-struct Layout {
-    int ldu, ldc;       // smem leading dims of the U and C slabs
+// Row-space products on a slab, tiled 4 rows x 4 output columns:
+// a1 = A1 S1 (K1 terms), a2 = A2 S2 (K2 terms); A1, A2 column-major (ld);
+// S1, S2 row-major with leading dimensions ls1, ls2; tri: S1 is upper
+// triangular (terms k > column skipped).  store(rc, cj, a1, a2) consumes
+// the tile of row chunk rc and column chunk cj.
+template <typename T, typename Store>
+__device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K1, const T *S1, int ls1,
+                                               const T *A2, int K2, const T *S2, int ls2, int ld, bool tri,
+                                               Store store) {
+    const int chunks = bm >> 2, tn = (N + 3) >> 2;
+    for (int tile = threadIdx.x; tile < chunks * tn; tile += blockDim.x) {
+        const int rc = tile % chunks, cj = tile / chunks;
+        T a1[4][4], a2[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a1[u][v] = a2[u][v] = (T)0;
+        const int k1end = tri ? min(K1, 4 * cj + 4) : K1;
+        for (int k = 0; k < k1end; ++k) {
+            T x[4], s[4];
+            lds4(A1 + (size_t)k * ld + 4 * rc, x);
+            lds4(S1 + (size_t)k * ls1 + 4 * cj, s);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) a1[u][v] = fma(x[u], s[v], a1[u][v]);
+        }
+        for (int k = 0; k < K2; ++k) {
+            T x[4], s[4];
+            lds4(A2 + (size_t)k * ld + 4 * rc, x);
+            lds4(S2 + (size_t)k * ls2 + 4 * cj, s);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) a2[u][v] = fma(x[u], s[v], a2[u][v]);
+        }
+        store(rc, cj, a1, a2);
+    }
+}
+
+// Sum of FP64 partials inside the kernel: the last CTA to arrive in each
+// group of RED_GROUP CTAs sums that group's partials; the last group to
+// finish sums the group results.  Orders are fixed by block index; arrival
+// counters are reset by the CTAs that consumed them.
+__device__ void tall_reduce(const double *part, double *gsum, double *out, int count, int64_t stride,
+                            unsigned *counters, int *s_flag) {
+    const int tid = threadIdx.x;
+    const int grid = gridDim.x;
+    const int ngroups = (grid + RED_GROUP - 1) / RED_GROUP;
+    const int grp = blockIdx.x / RED_GROUP;
+    const int gsize = min(RED_GROUP, grid - grp * RED_GROUP);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *s_flag = (atomicAdd(&counters[grp], 1u) == (unsigned)(gsize - 1));
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    for (int e = tid; e < count; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < gsize; ++b) s += __ldcg(part + (int64_t)(grp * RED_GROUP + b) * stride + e);
+        gsum[(int64_t)grp * stride + e] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        counters[grp] = 0;
+        *s_flag = (atomicAdd(&counters[ngroups], 1u) == (unsigned)(ngroups - 1));
+    }
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    for (int e = tid; e < count; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < ngroups; ++b) s += __ldcg(gsum + (int64_t)b * stride + e);
+        out[e] = s;
+    }
+    if (tid == 0) counters[ngroups] = 0;
+}
+
+struct SmemPlan {
+    int ld;          // slab leading dimension (bm + pad)
     int r4, c4;
+    size_t buf;      // one slab buffer (r4 + c4 columns), elements
+    size_t ws;       // W buffer, elements
+    size_t s1, s2, s3;
+    size_t acc1, acc2;   // doubles
 };
 
-__device__ __forceinline__ Layout layout_of(int rmax, int cmax) {
-    Layout L;
-    L.r4 = round4(rmax);
-    L.c4 = round4(cmax);
-    L.ldu = L.r4 + 4;
-    L.ldc = L.c4 + 4;
-    return L;
+__host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm) {
+    SmemPlan p;
+    p.ld = bm + 4;
+    p.r4 = round4(rmax);
+    p.c4 = round4(cmax);
+    p.buf = (size_t)(p.r4 + p.c4) * p.ld;
+    p.ws = (size_t)p.c4 * p.ld;
+    // S1: P (r x g) or X (r x rn); S2: P2 (r x g) or Y (g x rn); S3: M1 (g x g)
+    p.s1 = (size_t)p.r4 * (p.c4 > p.r4 ? p.c4 : p.r4);
+    p.s2 = (size_t)p.c4 * p.r4;
+    p.s3 = (size_t)p.c4 * p.c4;
+    p.acc1 = (size_t)p.r4 * p.c4;
+    p.acc2 = (size_t)p.c4 * p.c4;
+    return p;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_tall(int kind, TallArgs<T> a) {
+__host__ __device__ inline size_t smem_bytes(const SmemPlan &p) {
+    return (2 * p.buf + p.ws + p.s1 + p.s2 + p.s3) * sizeof(T) + (p.acc1 + p.acc2) * 8 +
+           (size_t)TALL_THREADS * 16 * sizeof(T) + 64;
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     const DevState *st = a.st;
     if (st->done) return;
     const int r = st->r_cur, g = st->g, rn = st->r_new;
-    const Layout L = layout_of(a.rmax, a.cmax);
     const int bm = a.bm;
+    const SmemPlan L = smem_plan(a.rmax, a.cmax, bm);
+    const int ld = L.ld;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Us = reinterpret_cast<T *>(smem_raw);                 // bm x ldu
-    T *Cs = Us + (size_t)bm * L.ldu;                         // bm x ldc
-    T *Ws = Cs + (size_t)bm * L.ldc;                         // bm x max(ldc, ldu)
-    const int ldw = L.ldc > L.ldu ? L.ldc : L.ldu;
-    const size_t sq = (size_t)(L.r4 + L.c4) * (L.r4 + L.c4);
-    T *S1 = Ws + (size_t)bm * ldw;                           // small operand 1
-    T *S2 = S1 + sq;                                         // small operand 2
-    T *S3 = S2 + sq;                                         // small operand 3 (c4 x c4)
-    double *acc1 = reinterpret_cast<double *>(S3 + (size_t)L.c4 * L.c4);
-    double *acc2 = acc1 + (size_t)L.r4 * L.c4;
-    T *red = reinterpret_cast<T *>(acc2 + (size_t)L.c4 * L.c4);
-
+    T *buf0 = reinterpret_cast<T *>(smem_raw);
+    T *buf1 = buf0 + L.buf;
+    T *Ws = buf1 + L.buf;
+    T *S1 = Ws + L.ws;
+    T *S2 = S1 + L.s1;
+    T *S3 = S2 + L.s2;
+    double *acc1 = reinterpret_cast<double *>(S3 + L.s3);
+    double *acc2 = acc1 + L.acc1;
+    T *red = reinterpret_cast<T *>(acc2 + L.acc2);
+    int *s_flag = reinterpret_cast<int *>(red + TALL_THREADS * 16);
     const int tid = threadIdx.x, bd = blockDim.x;
+    const int r4 = round4(r), g4 = round4(g), rn4 = round4(rn);
+    const bool vec = a.vec != 0;
+    const bool load_c = KIND != TALL_UPDATE || g > 0;
     auto ucol = [&](int l) { return a.U + (int64_t)l * a.ldu; };
     auto ccol = [&](int j) { return a.A + (int64_t)(a.idx ? a.idx[j] : j) * a.lda; };
 
-    // small operands -> shared (as T); accumulators -> 0
-    if (kind == TALL_CGS || kind == TALL_QR2) {
-        for (int e = tid; e < L.r4 * L.c4; e += bd) {
-            const int l = e / L.c4, j = e - l * L.c4;
+    // zero the padding columns of both buffers once; small operands -> shared
+    for (int b = 0; b < 2; ++b) {
+        T *Ub = b ? buf1 : buf0;
+        T *Cb = Ub + (size_t)L.r4 * ld;
+        for (int e = tid; e < (r4 - r) * ld; e += bd) Ub[(size_t)r * ld + e] = (T)0;
+        for (int e = tid; e < (g4 - g) * ld; e += bd) Cb[(size_t)g * ld + e] = (T)0;
+    }
+    if (KIND == TALL_CGS || KIND == TALL_QR2) {
+        for (int e = tid; e < r4 * g4; e += bd) {
+            const int l = e / g4, j = e - l * g4;
             S1[e] = (l < r && j < g) ? (T)a.P[l * a.cmax + j] : (T)0;
-            if (kind == TALL_QR2) S2[e] = (l < r && j < g) ? (T)a.P2[l * a.cmax + j] : (T)0;
+            if (KIND == TALL_QR2) S2[e] = (l < r && j < g) ? (T)a.P2[l * a.cmax + j] : (T)0;
         }
     }
-    if (kind == TALL_QR2) {
-        for (int e = tid; e < L.c4 * L.c4; e += bd) {
-            const int l = e / L.c4, j = e - l * L.c4;
+    if (KIND == TALL_QR2) {
+        for (int e = tid; e < g4 * g4; e += bd) {
+            const int l = e / g4, j = e - l * g4;
             S3[e] = (l < g && j < g && l <= j) ? (T)a.M1[l * a.cmax + j] : (T)0;
         }
+        for (int e = tid; e < (g4 - g) * ld; e += bd) Ws[(size_t)g * ld + e] = (T)0;
     }
-    if (kind == TALL_UPDATE) {
-        // X: r x rn (ld r4), Y: g x rn (ld r4)
-        for (int e = tid; e < L.r4 * L.r4; e += bd) {
-            const int l = e / L.r4, q = e - l * L.r4;
+    if (KIND == TALL_UPDATE) {
+        for (int e = tid; e < r4 * rn4; e += bd) {
+            const int l = e / rn4, q = e - l * rn4;
             S1[e] = (l < r && q < rn) ? (T)a.Xm[l * a.rmax + q] : (T)0;
         }
-        for (int e = tid; e < L.c4 * L.r4; e += bd) {
-            const int j = e / L.r4, q = e - j * L.r4;
+        for (int e = tid; e < g4 * rn4; e += bd) {
+            const int j = e / rn4, q = e - j * rn4;
             S2[e] = (j < g && q < rn) ? (T)a.Ym[j * a.rmax + q] : (T)0;
         }
     }
-    if (kind != TALL_UPDATE) {
-        for (int e = tid; e < L.r4 * L.c4; e += bd) acc1[e] = 0.0;
-        for (int e = tid; e < L.c4 * L.c4; e += bd) acc2[e] = 0.0;
+    if (KIND != TALL_UPDATE) {
+        for (int e = tid; e < (int)L.acc1; e += bd) acc1[e] = 0.0;
+        for (int e = tid; e < (int)L.acc2; e += bd) acc2[e] = 0.0;
     }
-    __syncthreads();
 
-    for (int64_t i0 = (int64_t)blockIdx.x * bm; i0 < a.m; i0 += (int64_t)gridDim.x * bm) {
-        const int rows = (int)((a.m - i0) < bm ? (a.m - i0) : bm);
-        load_slab<T>(Us, L.ldu, r, bm, rows, i0, ucol);
-        if (kind != TALL_UPDATE || g > 0) load_slab<T>(Cs, L.ldc, g, bm, rows, i0, ccol);
-        __syncthreads();
-        if (kind == TALL_PROJ) {
-            acc_xty<T>(Us, L.ldu, r, Cs, L.ldc, g, rows, false, acc1, L.c4, red);
-        } else if (kind == TALL_CGS || kind == TALL_QR2) {
-            // Z = C - U P  (then - U P2 for the QR2 pass), in place in Cs
-            if (r > 0) {
-                for (int e = tid; e < rows * g; e += bd) {
-                    const int i = e / g, j = e - i * g;
-                    T z = Cs[i * L.ldc + j];
-                    for (int l = 0; l < r; ++l) z = fma(-Us[i * L.ldu + l], S1[l * L.c4 + j], z);
-                    if (kind == TALL_QR2) {
-                        T z2 = (T)0;
-                        for (int l = 0; l < r; ++l) z2 = fma(Us[i * L.ldu + l], S2[l * L.c4 + j], z2);
-                        z -= z2;
-                    }
-                    Cs[i * L.ldc + j] = z;
-                }
-                __syncthreads();
-            }
-            if (kind == TALL_CGS) {
-                if (r > 0) acc_xty<T>(Us, L.ldu, r, Cs, L.ldc, g, rows, false, acc1, L.c4, red);
-                acc_xty<T>(Cs, L.ldc, g, Cs, L.ldc, g, rows, true, acc2, L.c4, red);
-            } else {
-                // W = Z M1 (M1 upper triangular)
-                for (int e = tid; e < rows * g; e += bd) {
-                    const int i = e / g, j = e - i * g;
-                    T w = (T)0;
-                    for (int l = 0; l <= j; ++l) w = fma(Cs[i * L.ldc + l], S3[l * L.c4 + j], w);
-                    Ws[i * L.ldc + j] = w;
-                }
-                for (int e = tid; e < rows * (L.c4 - g); e += bd) {
-                    const int i = e / (L.c4 - g), j = g + (e - i * (L.c4 - g));
-                    Ws[i * L.ldc + j] = (T)0;
-                }
-                __syncthreads();
-                acc_xty<T>(Ws, L.ldc, g, Ws, L.ldc, g, rows, true, acc2, L.c4, red);
-            }
-        } else {
-            // U_new rows = U X + C Y  -> Ws (bm x ldu), then coalesced write-back
-            for (int e = tid; e < rows * rn; e += bd) {
-                const int i = e / rn, q = e - i * rn;
-                T u = (T)0;
-                for (int l = 0; l < r; ++l) u = fma(Us[i * L.ldu + l], S1[l * L.r4 + q], u);
-                for (int j = 0; j < g; ++j) u = fma(Cs[i * L.ldc + j], S2[j * L.r4 + q], u);
-                Ws[i * L.ldu + q] = u;
-            }
-            __syncthreads();
-            for (int e = tid; e < rows * rn; e += bd) {
-                const int q = e / rows, i = e - q * rows;
-                a.U[(int64_t)q * a.ldu + i0 + i] = Ws[i * L.ldu + q];
-            }
-            __syncthreads();
-        }
+    const int64_t step = (int64_t)gridDim.x * bm;
+    int64_t i0 = (int64_t)blockIdx.x * bm;
+    if (i0 < a.m) {
+        issue_slab<T>(buf0, ld, r, bm, i0, a.m, vec, ucol, AllLive{});
+        if (load_c) issue_slab<T>(buf0 + (size_t)L.r4 * ld, ld, g, bm, i0, a.m, vec, ccol, AllLive{});
     }
-    if (kind == TALL_UPDATE) return;
-    // write this CTA's FP64 partial
+    cp_async_commit();
+    int b = 0;
+    for (; i0 < a.m; i0 += step, b ^= 1) {
+        T *Us = b ? buf1 : buf0;
+        T *Cs = Us + (size_t)L.r4 * ld;
+        const int64_t inext = i0 + step;
+        if (inext < a.m) {
+            T *Un = b ? buf0 : buf1;
+            issue_slab<T>(Un, ld, r, bm, inext, a.m, vec, ucol, AllLive{});
+            if (load_c) issue_slab<T>(Un + (size_t)L.r4 * ld, ld, g, bm, inext, a.m, vec, ccol, AllLive{});
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        if (KIND == TALL_PROJ) {
+            gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, L.c4, red);
+        } else if (KIND == TALL_CGS) {
+            if (r > 0) {
+                rowspace_tiles<T>(bm, g, Us, r, S1, g4, Us, 0, S2, g4, ld, false,
+                                  [&](int rc, int cj, T (&a1)[4][4], T (&)[4][4]) {
+#pragma unroll
+                                      for (int v = 0; v < 4; ++v) {
+                                          T *p = Cs + (size_t)(4 * cj + v) * ld + 4 * rc;
+                                          T z[4];
+                                          lds4(p, z);
+#pragma unroll
+                                          for (int u = 0; u < 4; ++u) z[u] -= a1[u][v];
+                                          sts4(p, z);
+                                      }
+                                  });
+                __syncthreads();
+                gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, L.c4, red);
+            }
+            gram_acc<T>(Cs, g, Cs, g, ld, bm, true, acc2, L.c4, red);
+        } else if (KIND == TALL_QR2) {
+            if (r > 0) {
+                rowspace_tiles<T>(bm, g, Us, r, S1, g4, Us, r, S2, g4, ld, false,
+                                  [&](int rc, int cj, T (&a1)[4][4], T (&a2)[4][4]) {
+#pragma unroll
+                                      for (int v = 0; v < 4; ++v) {
+                                          T *p = Cs + (size_t)(4 * cj + v) * ld + 4 * rc;
+                                          T z[4];
+                                          lds4(p, z);
+#pragma unroll
+                                          for (int u = 0; u < 4; ++u) z[u] = (z[u] - a1[u][v]) - a2[u][v];
+                                          sts4(p, z);
+                                      }
+                                  });
+                __syncthreads();
+            }
+            rowspace_tiles<T>(bm, g, Cs, g, S3, g4, Cs, 0, S3, g4, ld, true,
+                              [&](int rc, int cj, T (&a1)[4][4], T (&)[4][4]) {
+#pragma unroll
+                                  for (int v = 0; v < 4; ++v) {
+                                      T w[4];
+#pragma unroll
+                                      for (int u = 0; u < 4; ++u) w[u] = a1[u][v];
+                                      sts4(Ws + (size_t)(4 * cj + v) * ld + 4 * rc, w);
+                                  }
+                              });
+            __syncthreads();
+            gram_acc<T>(Ws, g, Ws, g, ld, bm, true, acc2, L.c4, red);
+        } else {
+            const int64_t rows_left = a.m - i0;
+            rowspace_tiles<T>(bm, rn, Us, r, S1, rn4, Cs, g, S2, rn4, ld, false,
+                              [&](int rc, int cj, T (&a1)[4][4], T (&a2)[4][4]) {
+#pragma unroll
+                                  for (int v = 0; v < 4; ++v) {
+                                      const int q = 4 * cj + v;
+                                      if (q >= rn) continue;
+                                      T o[4];
+#pragma unroll
+                                      for (int u = 0; u < 4; ++u) o[u] = a1[u][v] + a2[u][v];
+                                      T *dst = a.U + (int64_t)q * a.ldu + i0 + 4 * rc;
+                                      if (vec && rows_left >= 4 * rc + 4) {
+                                          sts4(dst, o);
+                                      } else {
+#pragma unroll
+                                          for (int u = 0; u < 4; ++u)
+                                              if (4 * rc + u < rows_left) dst[u] = o[u];
+                                      }
+                                  }
+                              });
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    if (KIND == TALL_UPDATE) return;
+    // this CTA's FP64 partial, then the in-kernel fixed-order sum
     double *out = a.part + (int64_t)blockIdx.x * a.part_stride;
-    if (kind == TALL_PROJ) {
+    if (KIND == TALL_PROJ) {
         for (int e = tid; e < r * g; e += bd) {
             const int l = e / g, j = e - l * g;
             out[l * a.cmax + j] = acc1[l * L.c4 + j];
         }
-    } else if (kind == TALL_CGS) {
+    } else if (KIND == TALL_CGS) {
         for (int e = tid; e < r * g; e += bd) {
             const int l = e / g, j = e - l * g;
             out[l * a.cmax + j] = acc1[l * L.c4 + j];
@@ -262,14 +462,16 @@ __global__ void __launch_bounds__(256) k_tall(int kind, TallArgs<T> a) {
             if (p <= q) out[p * a.cmax + q] = acc2[p * L.c4 + q];
         }
     }
+    tall_reduce(a.part, a.gsum, a.out, (int)a.part_stride, a.part_stride, a.counters, s_flag);
 }
 
 // ---------------------------------------------------------------------------
 // Y = A^T U.  CTA (blockIdx.x, blockIdx.y) owns nb columns of A and a range
-// of rows; writes its FP64 partial of the nb x r block of Y.
+// of rows; its FP64 partial of the nb x r block of Y is summed over the
+// row ranges by the last CTA of the column block to arrive.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_atu(AtuArgs<T> a, int nb, int bm) {
+__global__ void __launch_bounds__(TALL_THREADS) k_atu(AtuArgs<T> a, int nb, int bm) {
     const DevState *st = a.st;
     if (st->done) return;
     const int r = st->r_cur;
@@ -279,49 +481,73 @@ __global__ void __launch_bounds__(256) k_atu(AtuArgs<T> a, int nb, int bm) {
     const int64_t rows_per = ((a.m + split - 1) / split + bm - 1) / bm * bm;
     const int64_t ib = (int64_t)blockIdx.y * rows_per;
     const int64_t ie = (ib + rows_per) < a.m ? (ib + rows_per) : a.m;
-    const int nb4 = round4(nb), r4 = round4(r);
-    const int ldas = nb4 + 4, ldus = r4 + 4;
+    const int nb4 = round4(nb), r4 = round4(a.rmax);
+    const int ld = bm + 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *As = reinterpret_cast<T *>(smem_raw);
-    T *Us = As + (size_t)bm * ldas;
-    double *acc = reinterpret_cast<double *>(Us + (size_t)bm * ldus);
+    T *buf0 = reinterpret_cast<T *>(smem_raw);
+    const size_t bsz = (size_t)(nb4 + r4) * ld;
+    T *buf1 = buf0 + bsz;
+    double *acc = reinterpret_cast<double *>(buf1 + bsz);
     T *red = reinterpret_cast<T *>(acc + (size_t)nb4 * r4);
+    int *s_flag = reinterpret_cast<int *>(red + TALL_THREADS * 16);
     const int tid = threadIdx.x, bd = blockDim.x;
+    const bool vec = a.vec != 0;
     for (int e = tid; e < nb4 * r4; e += bd) acc[e] = 0.0;
     bool any = true;
     if (a.mask) {
         any = false;
         for (int c = 0; c < ncols; ++c) any |= a.mask[j0 + c] != 0;
     }
-    __syncthreads();
-    if (any && r > 0) {
-        auto acol = [&](int c) {
-            const bool live = !a.mask || a.mask[j0 + c];
-            return live ? a.A + (j0 + c) * a.lda : (const T *)nullptr;
-        };
-        auto ucol = [&](int l) { return a.U + (int64_t)l * a.ldu; };
-        for (int64_t i0 = ib; i0 < ie; i0 += bm) {
-            const int rows = (int)((ie - i0) < bm ? (ie - i0) : bm);
-            // A slab: masked-out columns are zero and not read
-            for (int e = tid; e < nb4 * bm; e += bd) {
-                const int c = e / bm, i = e - c * bm;
-                T v = (T)0;
-                if (c < ncols && i < rows) {
-                    const T *p = acol(c);
-                    if (p) v = p[i0 + i];
-                }
-                As[i * ldas + c] = v;
-            }
-            load_slab<T>(Us, ldus, r, bm, rows, i0, ucol);
-            __syncthreads();
-            acc_xty<T>(As, ldas, ncols, Us, ldus, r, rows, false, acc, r4, red);
-        }
+    for (int bb = 0; bb < 2; ++bb) {
+        T *Ab = bb ? buf1 : buf0;
+        T *Ub = Ab + (size_t)nb4 * ld;
+        for (int e = tid; e < (nb4 - ncols) * ld; e += bd) Ab[(size_t)ncols * ld + e] = (T)0;
+        for (int e = tid; e < (round4(r) - r) * ld; e += bd) Ub[(size_t)r * ld + e] = (T)0;
     }
+    __syncthreads();
+    if (any && r > 0 && ib < ie) {
+        auto acol = [&](int c) { return a.A + (j0 + c) * a.lda; };
+        auto ucol = [&](int l) { return a.U + (int64_t)l * a.ldu; };
+        auto live = [&](int c) { return a.mask == nullptr || a.mask[j0 + c] != 0; };
+        auto issue = [&](T *dst, int64_t i0) {
+            issue_slab<T>(dst, ld, ncols, bm, i0, ie, vec, acol, live);
+            issue_slab<T>(dst + (size_t)nb4 * ld, ld, r, bm, i0, ie, vec, ucol, AllLive{});
+        };
+        issue(buf0, ib);
+        cp_async_commit();
+        int b = 0;
+        for (int64_t i0 = ib; i0 < ie; i0 += bm, b ^= 1) {
+            T *As = b ? buf1 : buf0;
+            if (i0 + bm < ie) issue(b ? buf0 : buf1, i0 + bm);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            gram_acc<T>(As, ncols, As + (size_t)nb4 * ld, r, ld, bm, false, acc, r4, red);
+        }
+        cp_async_wait<0>();
+    }
+    __syncthreads();
+    // partial: column-major n x r (ld n) per row range
     double *out = a.part + (int64_t)blockIdx.y * a.n * a.rmax;
     for (int e = tid; e < ncols * r; e += bd) {
         const int l = e / ncols, c = e - l * ncols;
         out[(int64_t)l * a.n + j0 + c] = acc[c * r4 + l];
     }
+    // the last of the `split` CTAs of this column block sums them
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *s_flag = (atomicAdd(&a.counters[blockIdx.x], 1u) == (unsigned)(split - 1));
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    for (int e = tid; e < ncols * r; e += bd) {
+        const int l = e / ncols, c = e - l * ncols;
+        double s = 0.0;
+        for (int y = 0; y < split; ++y)
+            s += __ldcg(a.part + (int64_t)y * a.n * a.rmax + (int64_t)l * a.n + j0 + c);
+        a.Y[(int64_t)l * a.n + j0 + c] = s;
+    }
+    if (tid == 0) a.counters[blockIdx.x] = 0;
 }
 
 // sign-reference dots: d_l = sum_i U_il z_i
@@ -343,52 +569,65 @@ __global__ void __launch_bounds__(256) k_sign_dots(const T *U, int64_t m, int64_
     }
 }
 
+template <typename T, int KIND>
+pod_status launch_kind(const TallArgs<T> &a, const TallPlan &plan, cudaStream_t st) {
+    POD_CUDA_TRY(cudaFuncSetAttribute(k_tall<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)plan.smem));
+    k_tall<T, KIND><<<plan.grid, TALL_THREADS, plan.smem, st>>>(a);
+    POD_CUDA_TRY(cudaGetLastError());
+    return POD_OK;
+}
+
 }  // namespace
 
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
-    TallPlan p;
-    const size_t es = dtype == POD_F32 ? 4 : 8;
-    const int r4 = round4(rmax), c4 = round4(cmax);
-    const int ldu = r4 + 4, ldc = c4 + 4;
-    const int ldw = ldc > ldu ? ldc : ldu;
-    const size_t small_t = (size_t)(r4 + c4) * (r4 + c4) * 2 + (size_t)c4 * c4;
-    const size_t accs = ((size_t)r4 * c4 + (size_t)c4 * c4) * 8;
-    const size_t red = 256 * 16 * es;
-    // two CTAs per SM when the slab allows it
-    int bm = 128;
-    for (; bm > 16; bm >>= 1) {
-        size_t tot = (size_t)bm * (ldu + ldc + (size_t)ldw) * es + small_t * es + accs + red;
-        if (tot <= 110 * 1024) break;
+    TallPlan p{};
+    const bool f32 = dtype == POD_F32;
+    auto bytes_for = [&](int bm) {
+        SmemPlan L = smem_plan(rmax, cmax, bm);
+        return f32 ? smem_bytes<float>(L) : smem_bytes<double>(L);
+    };
+    // prefer two resident CTAs per SM (16 warps), then the largest slab
+    int bm = 0, per_sm = 2;
+    for (int b = 128; b >= 32 && !bm; b >>= 1)
+        if (bytes_for(b) <= 110 * 1024) bm = b;
+    if (!bm) {
+        per_sm = 1;
+        for (int b = 128; b >= 16 && !bm; b >>= 1)
+            if (bytes_for(b) <= 200 * 1024) bm = b;
+        if (!bm) bm = 16;
     }
     p.bm = bm;
-    const size_t base = (size_t)bm * (ldu + ldc + (size_t)ldw) * es + small_t * es + accs + red;
-    for (int k = 0; k < 4; ++k) p.smem[k] = base;
+    p.smem = bytes_for(bm);
     const int64_t slabs = (m + bm - 1) / bm;
-    int64_t grid = 2 * (int64_t)num_sms;
+    int64_t grid = (int64_t)per_sm * num_sms;
     if (grid > slabs) grid = slabs;
     if (grid < 1) grid = 1;
     p.grid = (int)grid;
+    p.groups = (p.grid + RED_GROUP - 1) / RED_GROUP;
     return p;
 }
 
 template <typename T>
 pod_status launch_tall(TallKind kind, const TallArgs<T> &a, const TallPlan &plan, cudaStream_t st) {
-    const size_t smem = plan.smem[kind];
-    POD_CUDA_TRY(cudaFuncSetAttribute(k_tall<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tall<T><<<plan.grid, 256, smem, st>>>((int)kind, a);
-    POD_CUDA_TRY(cudaGetLastError());
-    return POD_OK;
+    if (plan.smem > 227 * 1024) return POD_EUNSUPPORTED;
+    switch (kind) {
+        case TALL_PROJ: return launch_kind<T, TALL_PROJ>(a, plan, st);
+        case TALL_CGS: return launch_kind<T, TALL_CGS>(a, plan, st);
+        case TALL_QR2: return launch_kind<T, TALL_QR2>(a, plan, st);
+        default: return launch_kind<T, TALL_UPDATE>(a, plan, st);
+    }
 }
 
 AtuPlan atu_plan(int dtype, int64_t m, int64_t n, int rmax, int num_sms) {
-    AtuPlan p;
+    AtuPlan p{};
     const size_t es = dtype == POD_F32 ? 4 : 8;
     p.nb = 32;
     p.bm = 128;
     const int nb4 = round4(p.nb), r4 = round4(rmax);
     for (;;) {
-        p.smem = (size_t)p.bm * ((nb4 + 4) + (r4 + 4)) * es + (size_t)nb4 * r4 * 8 + 256 * 16 * es;
-        if (p.smem <= 200 * 1024 || p.bm <= 16) break;
+        p.smem = 2 * (size_t)(nb4 + r4) * (p.bm + 4) * es + (size_t)nb4 * r4 * 8 + TALL_THREADS * 16 * es + 64;
+        if (p.smem <= 110 * 1024 || p.bm <= 16) break;
         p.bm >>= 1;
     }
     const int64_t cb = (n + p.nb - 1) / p.nb;
@@ -405,7 +644,7 @@ AtuPlan atu_plan(int dtype, int64_t m, int64_t n, int rmax, int num_sms) {
 template <typename T>
 pod_status launch_atu(const AtuArgs<T> &a, const AtuPlan &plan, cudaStream_t st) {
     POD_CUDA_TRY(cudaFuncSetAttribute(k_atu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem));
-    k_atu<T><<<plan.grid, 256, plan.smem, st>>>(a, plan.nb, plan.bm);
+    k_atu<T><<<plan.grid, TALL_THREADS, plan.smem, st>>>(a, plan.nb, plan.bm);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }

@@ -28,11 +28,10 @@ POD_CORE_AUTO, POD_CORE_F32, POD_CORE_F64 = 0, 1, 2
 
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
-            "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters"]
+            "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats"]
 
-ROUND_KERNELS = ["sample", "proj", "proj_sum", "cgs_gram", "cgs_sum", "chol1", "qr2_gram", "qr2_sum",
-                 "core_svd", "update", "finish"]
-ORT_KERNELS = ["ort_atu", "ort_sum", "ort_values"]
+ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "core_svd", "update", "finish"]
+ORT_KERNELS = ["ort_atu", "ort_values"]
 
 
 class PodParams(ctypes.Structure):
@@ -81,6 +80,7 @@ def lib():
         L.pod_reset.argtypes = [vp, vp]
         L.pod_round_timings.argtypes = [vp, P(ctypes.c_float), i32, P(i32)]
         L.pod_counters.argtypes = [vp, P(i64), P(i32)]
+        L.pod_core_stats.argtypes = [vp, P(i32), P(i64)]
         for name in EXPORTED:
             if name not in ("pod_destroy", "pod_strerror"):
                 getattr(L, name).restype = ctypes.c_int
@@ -229,6 +229,13 @@ class Context:
         rounds = ctypes.c_int32(0)
         _check(lib().pod_counters(self._h, ctypes.byref(launches), ctypes.byref(rounds)), "pod_counters")
         return int(launches.value), int(rounds.value)
+
+    def core_stats(self):
+        """(Jacobi sweeps, clock cycles per phase) of the last core SVD."""
+        sw = ctypes.c_int32(0)
+        cyc = (ctypes.c_int64 * 6)()
+        _check(lib().pod_core_stats(self._h, ctypes.byref(sw), cyc), "pod_core_stats")
+        return int(sw.value), [int(x) for x in cyc]
 
     def trace(self, t: int):
         idx = (ctypes.c_int32 * self.params.c)()
