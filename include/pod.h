@@ -256,6 +256,31 @@ POD_API pod_status pod_block_merge(int32_t dtype, int64_t m, const void *U1_dev,
                            void *U_out_dev, double *s_out_dev, int32_t *r_out_host,
                            void *stream);
 
+/*
+ * pod_sample_noalloc -- the same draw step as pod_sample (same inputs, same
+ * outputs, bit-identical results), for callers that cannot allocate device
+ * memory: host or stream callbacks (where CUDA API calls that may allocate
+ * are not allowed), processes whose device memory pool is capped or fully
+ * reserved by another framework, and latency-critical loops that must not
+ * touch the allocator.  It makes no allocation of any kind: its scratch
+ * lives in fixed arrays compiled into the library, which every GPU that
+ * loads the library holds (about 1.1 MB) until the process exits.
+ * The paper has no counterpart to this entry point.
+ *   Limits: n <= 65536 columns and c <= 4096 draws; larger sizes return
+ *   POD_EUNSUPPORTED without doing anything.
+ *   The first call on each device looks up the arrays' device addresses
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   outside any stream capture.
+ *   All calls share the arrays: calls that overlap on the GPU (different
+ *   streams or host threads on one device) race and must be serialised by
+ *   the caller.  Each call re-initialises the parts it needs.
+ * Arguments, layout and errors as pod_sample.  Stream-ordered, does not
+ * synchronise.
+ */
+POD_API pod_status pod_sample_noalloc(const uint64_t *w_dev, uint8_t *mask_dev, int64_t n, int32_t c,
+                                      uint64_t seed, int32_t t, int32_t stream_id, int32_t *idx_dev,
+                                      int32_t *g_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

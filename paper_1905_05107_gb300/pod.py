@@ -28,7 +28,8 @@ POD_CORE_AUTO, POD_CORE_F32, POD_CORE_F64 = 0, 1, 2
 
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
-            "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats"]
+            "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
+            "pod_sample_noalloc"]
 
 ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "core_svd", "update", "finish"]
 ORT_KERNELS = ["ort_atu", "ort_values"]
@@ -81,6 +82,7 @@ def lib():
         L.pod_round_timings.argtypes = [vp, P(ctypes.c_float), i32, P(i32)]
         L.pod_counters.argtypes = [vp, P(i64), P(i32)]
         L.pod_core_stats.argtypes = [vp, P(i32), P(i64)]
+        L.pod_sample_noalloc.argtypes = [vp, vp, i64, i32, u64, i32, i32, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("pod_destroy", "pod_strerror"):
                 getattr(L, name).restype = ctypes.c_int
