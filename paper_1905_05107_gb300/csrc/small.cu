@@ -16,6 +16,7 @@
 namespace {
 
 constexpr int SMALL_THREADS = 1024;
+constexpr int CORE_THREADS = 512;
 
 __device__ __forceinline__ double unit_roundoff(int dtype) {
     return dtype == POD_F32 ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
@@ -148,6 +149,10 @@ __device__ int jacobi_hw_n(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *
     const int lane = tid & 31, half = lane >> 4, l16 = lane & 15, warp = tid >> 5, nw = bd >> 5;
     const int N = ncol + (ncol & 1), npairs = N / 2, M = N - 1;
     const J tol2 = tol * tol;
+    // a sweep whose largest relative off-diagonal g^2 / (alpha_p alpha_q) stays
+    // below loose2 leaves every pair below tol after its own rotations
+    // (quadratic convergence), so the all-quiet check sweep is skipped
+    const J loose2 = (J)16 * tol;
     int sweep = 0;
     for (;; ++sweep) {
         for (int c = tid; c < ncol; c += bd) {
@@ -199,6 +204,7 @@ __device__ int jacobi_hw_n(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *
                 for (int o = 8; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, 16);
                 if (valid) {
                     const J a = alpha[p], b = alpha[q];
+                    if (a > (J)0 && b > (J)0 && g * g > loose2 * loose2 * a * b && l16 == 0) s_flag[1] = 1;
                     if (a > (J)0 && b > (J)0 && g * g > tol2 * a * b) {
                         const J zeta = j_div(b - a, g + g);
                         const J az = fabs(zeta);
@@ -233,9 +239,20 @@ __device__ int jacobi_hw_n(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *
             }
             __syncthreads();
         }
-        const int rotated = *s_flag;
+        const int rotated = s_flag[0], big = s_flag[1];
         __syncthreads();
+        if (tid == 0) s_flag[1] = 0;
         if (!rotated) break;
+        if (!big) {
+            ++sweep;
+            for (int c = tid; c < ncol; c += bd) {
+                J s = 0;
+                for (int i = 0; i < nrow; ++i) s = fma(B[(size_t)c * ldb + i], B[(size_t)c * ldb + i], s);
+                alpha[c] = s;
+            }
+            __syncthreads();
+            break;
+        }
     }
     return sweep;
 }
@@ -459,7 +476,9 @@ __host__ __device__ inline CoreLayout core_layout(int rmax, int cmax, int jsize)
     CoreLayout L;
     const int nmax = rmax + cmax;
     L.keep = al16x((size_t)nmax * nmax * 8) + al16x((size_t)cmax * cmax * 8) + al16x((size_t)rmax * cmax * 8);
-    L.phaseA = 5 * al16x((size_t)cmax * cmax * 8);
+    // FP32 path: 3 X + 8 float g x g arrays; FP64 path: 5 X arrays
+    L.phaseA = jsize == 4 ? 3 * al16x((size_t)cmax * cmax * 8) + 8 * al16x((size_t)cmax * cmax * 4)
+                          : 5 * al16x((size_t)cmax * cmax * 8);
     L.phaseB = 2 * al16x((size_t)nmax * nmax * jsize) + al16x((size_t)nmax * jsize) + al16x((size_t)nmax * 4);
     // Vr, Q, Yt: nmax x rmax X; Gb, Rb, Mw, Mb: rmax x rmax X; Bs: nmax x rmax J;
     // BtB: rmax^2 J; xv, yv: rmax J; sig: rmax X; ord2: rmax int
@@ -476,14 +495,14 @@ size_t core_smem_bytes(int rmax, int cmax, int dtype) {
 }
 
 template <typename X, typename J>
-__global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
+__global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     DevState *st = a.st;
     if (st->done) return;
     const int r = st->r_cur, g = st->g, nc = r + g, t = st->t;
     const int ld = a.cmax, nmax = a.rmax + a.cmax;
     const int tid = threadIdx.x, bd = blockDim.x;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_flag;
+    __shared__ int s_flag[2];
     __shared__ double red[32];
     __shared__ int s_rnew;
     __shared__ double s_measure, s_sin, s_cos;
@@ -502,7 +521,145 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
     unsigned char *work = smem_raw + CL.keep;
 
     // ---- phase A: R2 = chol(G2), M2 = R2^{-1}, R = R2 R1p, Rinv = M1 M2, E
-    {
+    if (sizeof(J) == 4) {
+        // FP32 path.  G2 = W^T W with W = Z M1 nearly orthonormal, so when
+        // |G2 - I| < 0.1 on the kept indices, R2 and R2^{-1} come from Newton
+        // steps R <- R + T(G2 - R^T R) (T: upper triangle, diagonal halved)
+        // and X <- X (2I - R2 X) from I, each step a parallel triangular
+        // product; otherwise a double-float Cholesky.  R = R2 R1p and
+        // R^{-1} = M1 M2 need only FP32 relative accuracy.
+        Carve cv{work};
+        X *W = cv.take<X>((size_t)ld * ld);
+        X *R2x = cv.take<X>((size_t)ld * ld);
+        X *M2x = cv.take<X>((size_t)ld * ld);
+        float *Gf = cv.take<float>((size_t)ld * ld);
+        float *R2f = cv.take<float>((size_t)ld * ld);
+        float *M2f = cv.take<float>((size_t)ld * ld);
+        float *T1 = cv.take<float>((size_t)ld * ld);
+        float *R1f = cv.take<float>((size_t)ld * ld);
+        float *M1f = cv.take<float>((size_t)ld * ld);
+        float *Rf = cv.take<float>((size_t)ld * ld);
+        float *Rif = cv.take<float>((size_t)ld * ld);
+        double dev = 0.0, dmax = 0.0;
+        for (int e = tid; e < g * g; e += bd) {
+            const int i = e / g, j = e % g;
+            const double gij = i <= j ? a.G2[i * ld + j] : a.G2[j * ld + i];
+            Gf[i * ld + j] = (float)gij;
+            R1f[i * ld + j] = (float)a.R1p[i * ld + j];
+            M1f[i * ld + j] = (float)a.M1[i * ld + j];
+            const bool kept = a.G2[i * ld + i] != 0.0 && a.G2[j * ld + j] != 0.0;
+            if (kept) {
+                const double d = fabs(gij - (i == j ? 1.0 : 0.0));
+                dev = d > dev ? d : dev;
+            }
+            if (i == j) dmax = gij > dmax ? gij : dmax;
+        }
+        for (int e = tid; e < r * g; e += bd) {
+            const int l = e / g, j = e % g;
+            Ptx[l * ld + j] = XOps<X>::from(a.Ptot[l * ld + j]);
+        }
+        dev = block_max<double>(dev, red);
+        dmax = block_max<double>(dmax, red);
+        if (dev < 0.1) {
+            for (int e = tid; e < g * g; e += bd) {
+                const int i = e / g, j = e % g;
+                const bool kept = Gf[i * ld + i] != 0.f;
+                R2f[i * ld + j] = (i == j && kept) ? 1.f : 0.f;
+                M2f[i * ld + j] = (i == j && kept) ? 1.f : 0.f;
+            }
+            __syncthreads();
+            for (int it = 0; it < 3; ++it) {
+                // T1 = G2 - R2^T R2 (upper part)
+                for (int e = tid; e < g * g; e += bd) {
+                    const int i = e / g, j = e % g;
+                    float v = 0.f;
+                    if (i <= j) {
+                        float acc = Gf[i * ld + j];
+                        for (int l = 0; l <= i; ++l) acc = fmaf(-R2f[l * ld + i], R2f[l * ld + j], acc);
+                        v = acc;
+                    }
+                    T1[i * ld + j] = v;
+                }
+                __syncthreads();
+                for (int e = tid; e < g * g; e += bd) {
+                    const int i = e / g, j = e % g;
+                    if (i <= j && Gf[i * ld + i] != 0.f && Gf[j * ld + j] != 0.f)
+                        R2f[i * ld + j] += (i == j) ? 0.5f * T1[i * ld + j] : T1[i * ld + j];
+                }
+                __syncthreads();
+            }
+            for (int it = 0; it < 3; ++it) {
+                // T1 = 2I - R2 M2 ; M2 <- M2 T1   (all upper triangular)
+                for (int e = tid; e < g * g; e += bd) {
+                    const int i = e / g, j = e % g;
+                    float v = 0.f;
+                    if (i <= j) {
+                        float acc = 0.f;
+                        for (int l = i; l <= j; ++l) acc = fmaf(R2f[i * ld + l], M2f[l * ld + j], acc);
+                        v = (i == j && Gf[i * ld + i] != 0.f ? 2.f : 0.f) - acc;
+                    }
+                    T1[i * ld + j] = v;
+                }
+                __syncthreads();
+                for (int e = tid; e < g * g; e += bd) {
+                    const int i = e / g, j = e % g;
+                    float v = 0.f;
+                    if (i <= j)
+                        for (int l = i; l <= j; ++l) v = fmaf(M2f[i * ld + l], T1[l * ld + j], v);
+                    Rf[i * ld + j] = v;   // scratch
+                }
+                __syncthreads();
+                for (int e = tid; e < g * g; e += bd) M2f[(e / g) * ld + e % g] = Rf[(e / g) * ld + e % g];
+                __syncthreads();
+            }
+        } else {
+            const double eps = nc * u;
+            const X thr = XOps<X>::from(eps * eps * dmax);
+            for (int e = tid; e < g * g; e += bd) {
+                const int i = e / g, j = e % g;
+                W[i * ld + j] = XOps<X>::from(i <= j ? a.G2[i * ld + j] : 0.0);
+            }
+            __syncthreads();
+            chol_drop<X>(W, ld, g, thr, R2x, ld, piv3);
+            tri_inv<X>(R2x, ld, g, W, ld, M2x, ld, dinv);
+            for (int e = tid; e < g * g; e += bd) {
+                const int i = e / g, j = e % g;
+                R2f[i * ld + j] = x_hi(R2x[i * ld + j]);
+                M2f[i * ld + j] = x_hi(M2x[i * ld + j]);
+            }
+            __syncthreads();
+        }
+        // R = R2 R1p, Rinv = M1 M2
+        for (int e = tid; e < g * g; e += bd) {
+            const int i = e / g, j = e % g;
+            float v = 0.f, w = 0.f;
+            if (i <= j)
+                for (int l = i; l <= j; ++l) {
+                    v = fmaf(R2f[i * ld + l], R1f[l * ld + j], v);
+                    w = fmaf(M1f[i * ld + l], M2f[l * ld + j], w);
+                }
+            Rf[i * ld + j] = v;
+            Rif[i * ld + j] = w;
+        }
+        __syncthreads();
+        for (int e = tid; e < g * g; e += bd) {
+            const int i = e / g, j = e % g;
+            Rinv[i * ld + j] = XOps<X>::from_f(Rif[i * ld + j]);
+        }
+        for (int e = tid; e < nc * nc; e += bd) {
+            const int q = e / nc, p = e % nc;   // column q, row p
+            X v = XOps<X>::zero();
+            if (p < r) {
+                if (q < r) v = (p == q) ? XOps<X>::from(a.sigma[p]) : XOps<X>::zero();
+                else v = Ptx[p * ld + (q - r)];
+            } else if (q >= r) {
+                v = XOps<X>::from_f(Rf[(p - r) * ld + (q - r)]);
+            }
+            if (!isfinite(x_hi(v))) s_bad = 1;
+            Ex[q * nc + p] = v;
+        }
+        __syncthreads();
+    } else {
         Carve cv{work};
         X *W = cv.take<X>((size_t)ld * ld);
         X *R2 = cv.take<X>((size_t)ld * ld);
@@ -575,7 +732,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_core(SmallArgs a) {
     const J eps_j = f32 ? (J)1.1920928955078125e-07 : (J)2.220446049250313e-16;
     const J tol = (J)2 * sqrt((J)nc) * eps_j;
     clk[1] = clock64();
-    const int nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, f32 ? 20 : 30, &s_flag);
+    if (tid == 0) s_flag[1] = 0;
+    const int nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, f32 ? 20 : 30, s_flag);
     clk[2] = clock64();
     sort_desc<J>(alpha, nc, order);
     const int rsel = a.r < nc ? a.r : nc;
@@ -741,10 +899,10 @@ pod_status launch_core(const SmallArgs &a, cudaStream_t s) {
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     if (!f64) {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_core<dfloat, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_core<dfloat, float><<<1, SMALL_THREADS, smem, s>>>(a);
+        k_core<dfloat, float><<<1, CORE_THREADS, smem, s>>>(a);
     } else {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_core<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_core<double, double><<<1, SMALL_THREADS, smem, s>>>(a);
+        k_core<double, double><<<1, CORE_THREADS, smem, s>>>(a);
     }
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
@@ -816,11 +974,12 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
     double *V = cv.take<double>((size_t)r * r);
     double *alpha = cv.take<double>(r);
     int *order = cv.take<int>(r);
-    __shared__ int s_flag;
+    __shared__ int s_flag[2];
     __shared__ double red[32];
     __shared__ double piv3[3];
     __shared__ double dinv[256];
     const int tid = threadIdx.x, bd = blockDim.x;
+    if (tid == 0) s_flag[1] = 0;
     double dmax = 0.0;
     for (int j = tid; j < r; j += bd) dmax = a.G2[j * r + j] > dmax ? a.G2[j * r + j] : dmax;
     dmax = block_max<double>(dmax, red);
@@ -842,7 +1001,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
         V[q * r + p] = (p == q) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_hw<double>(B, r, r, r, V, r, alpha, 2.0 * sqrt((double)r) * 2.220446049250313e-16, 40, &s_flag);
+    jacobi_hw<double>(B, r, r, r, V, r, alpha, 2.0 * sqrt((double)r) * 2.220446049250313e-16, 40, s_flag);
     sort_desc<double>(alpha, r, order);
     // sigma_s, V_R[:, s], U_R[:, s] = B[:, order[s]] / sigma_s, K = R^{-1} U_R
     for (int s = tid; s < r; s += bd) a.sigma[s] = sqrt(alpha[order[s]]);
