@@ -69,9 +69,14 @@ typedef struct pod_params {
     int64_t m, n, lda;     /* A is m x n, column-major, lda >= m             */
     int32_t k;             /* modes wanted, 1 <= k <= min(m, n)              */
     int32_t c;             /* column draws per iteration (with replacement)  */
-    int32_t w;             /* row draws per iteration when rows = 1          */
+    int32_t w;             /* row draws per iteration when rows = 1; 0 ->
+                              Eq. 5 with epsilon = delta = 0.6, at most m    */
     int32_t r;             /* carried rank after each merge; 0 -> k; r >= k  */
-    int32_t rows;          /* 0 = columns only (ICS), 1 = columns+rows (ICRS)*/
+    int32_t rows;          /* 0 = columns only (ICS), 1 = columns+rows (ICRS):
+                              the new block is C = D V_r, V_r the top r right
+                              singular vectors of the scaled row sample W of
+                              D (GET UPDATE with rows, SAMPLE AND SCALE
+                              UNIQUE ROWS); needs c <= 96                    */
     int32_t col_strategy;  /* POD_L2N | POD_UNF | POD_ORT                    */
     int32_t row_strategy;  /* POD_ROW_L2N | POD_ROW_LS                       */
     int32_t criterion;     /* POD_SUBSPACE | POD_MODES                       */
@@ -143,6 +148,24 @@ POD_API pod_status pod_modes(pod_ctx *ctx, void *U_dev, double *sigma_dev, void 
  */
 POD_API pod_status pod_get_trace(pod_ctx *ctx, int32_t t, int32_t *idx_host,
                          int32_t *g_host, double *measure_host);
+
+/*
+ * pod_last_rows -- the row sample of the most recent ICRS iteration (SAMPLE
+ * AND SCALE UNIQUE ROWS of Algorithm 1): the h distinct rows I_r in
+ * ascending order and their draw counts t_hat (sum = w).  Synchronises.
+ *   rows_host, counts_host : host arrays of cap entries (each may be NULL).
+ *   h                      : (host) receives h; 0 before the first round.
+ * Errors: POD_ESTATE when rows = 0, POD_EINVAL when h > cap (h is still
+ * written), POD_ECUDA.
+ */
+POD_API pod_status pod_last_rows(pod_ctx *ctx, int32_t *rows_host, int32_t *counts_host,
+                                 int32_t cap, int32_t *h);
+
+/*
+ * pod_row_draws -- the number w of row draws per iteration this context
+ * uses (p->w, or the Eq. 5 default); 0 when rows = 0.  No GPU work.
+ */
+POD_API pod_status pod_row_draws(pod_ctx *ctx, int32_t *w);
 
 /*
  * pod_replay_indices -- freeze the draws: iteration t merges exactly the

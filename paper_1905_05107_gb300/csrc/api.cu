@@ -4,6 +4,7 @@
 // whose sizes live in device memory (DevState); it is captured once into a
 // CUDA graph and replayed, and the host reads the 80-byte state only between
 // batches of rounds.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -14,6 +15,8 @@
 
 
 namespace {
+
+constexpr int ROW_KERNELS = 9;   // launches of launch_rows
 
 template <typename T>
 __global__ void k_write_modes(const T *U, int64_t m, int r_cur, int k, const double *sigma,
@@ -106,6 +109,16 @@ struct pod_ctx {
     double *rG, *rG2, *rM1, *rR1p, *rsig, *rVR, *rK, *dots, *part_sign;
     int32_t *replay_idx, *replay_off;
     int replay_T;
+    // ICRS (rows = 1): row sampling buffers, the scaled row block W (ldw x
+    // cmax), its Gram G_W, the coefficients V_r and the new block C = D V_r
+    int wdraws, ldw, rnb;
+    TallPlan wplan;
+    double *r_val, *r_bmax, *r_rscale, *GW, *rYm, *part_w, *gsum_w;
+    unsigned long long *r_bsum, *r_boff, *r_total;
+    uint64_t *r_w, *r_cdf;
+    unsigned *r_cnt, *counters_w;
+    int32_t *r_rows, *r_rcnt, *r_h;
+    void *Wrows, *Cbuf;
     // host
     DevState *hstate;   // pinned mirror
     cudaGraphExec_t graph;
@@ -133,7 +146,10 @@ static void ctx_free(pod_ctx *c) {
                     c->idx, c->hist_idx, c->hist_g, c->hist_measure, c->st, c->aux, c->part,
                     c->part_atu, c->P, c->PG, c->G2, c->Ptot, c->M1, c->R1p, c->E, c->Xm, c->Ym,
                     c->rG, c->rG2, c->rM1, c->rR1p, c->rsig, c->rVR, c->rK, c->dots, c->part_sign,
-                    c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters};
+                    c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
+                    c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
+                    c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
+                    c->r_rcnt, c->r_h, c->Wrows, c->Cbuf};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->hstate) cudaFreeHost(c->hstate);
@@ -152,10 +168,20 @@ static pod_status check_params(const pod_params *p) {
     if (p->col_strategy < POD_L2N || p->col_strategy > POD_ORT) return POD_EINVAL;
     if (p->criterion != POD_SUBSPACE && p->criterion != POD_MODES) return POD_EINVAL;
     if (p->core < POD_CORE_AUTO || p->core > POD_CORE_F64) return POD_EINVAL;
-    if (p->rows != 0) return POD_EUNSUPPORTED;
+    if (p->rows != 0 && p->rows != 1) return POD_EINVAL;
+    if (p->row_strategy != POD_ROW_L2N && p->row_strategy != POD_ROW_LS) return POD_EINVAL;
+    if (p->w < 0) return POD_EINVAL;
     if (p->c > 256 || (p->r > 0 ? p->r : p->k) > 256) return POD_EUNSUPPORTED;
     if (!(p->tol == p->tol)) return POD_EINVAL;
     return POD_OK;
+}
+
+// Default row draws of ICRS: Eq. 5 with epsilon = delta = 0.6, at most m.
+static int64_t default_row_draws(int64_t k, int64_t m) {
+    const double eps = 0.6, delta = 0.6;
+    const double v = ceil((double)(k * k) * pow(1.0 + sqrt(log(2.0 / delta)), 2.0) / pow(eps, 4.0));
+    const int64_t w = (int64_t)v;
+    return w < m ? w : m;
 }
 
 template <typename T>
@@ -266,6 +292,83 @@ static pod_status enqueue_round(pod_ctx *c) {
     mark(c);
 
     TallArgs<T> ta = tall_args<T>(c, c->part, (int64_t)c->rmax * c->cmax);
+    if (c->p.rows) {
+        // GET UPDATE with rows: W from sampled rows of D, V_r from W^T W,
+        // then the merge takes the materialised block C = D V_r
+        RowArgs<T> ra{};
+        ra.m = c->p.m;
+        ra.A = (const T *)c->A;
+        ra.lda = c->p.lda;
+        ra.idx = c->idx;
+        ra.U = (const T *)c->U;
+        ra.ldu = c->p.m;
+        ra.st = c->st;
+        ra.k = c->p.k;
+        ra.row_strategy = c->p.row_strategy;
+        ra.L = weight_bits(c->p.m);
+        ra.nblocks = c->rnb;
+        ra.wdraws = c->wdraws;
+        ra.ldw = c->ldw;
+        ra.cmax = c->cmax;
+        ra.seed = c->p.seed;
+        ra.stw = c->aux + 4;
+        ra.val = c->r_val;
+        ra.bmax = c->r_bmax;
+        ra.w = c->r_w;
+        ra.bsum = c->r_bsum;
+        ra.boff = c->r_boff;
+        ra.total = c->r_total;
+        ra.cdf = c->r_cdf;
+        ra.cnt = c->r_cnt;
+        ra.rows = c->r_rows;
+        ra.rcnt = c->r_rcnt;
+        ra.rscale = c->r_rscale;
+        ra.h = c->r_h;
+        ra.W = (T *)c->Wrows;
+        POD_TRY(launch_rows<T>(ra, s, c->sms));
+        c->launches += ROW_KERNELS - 1;
+        mark(c);
+        TallArgs<T> wa{};
+        wa.m = c->wdraws;
+        wa.A = (const T *)c->Wrows;
+        wa.lda = c->ldw;
+        wa.idx = nullptr;
+        wa.U = (T *)c->Wrows;
+        wa.ldu = c->ldw;
+        wa.st = c->aux + 4;
+        wa.rmax = c->cmax;
+        wa.cmax = c->cmax;
+        wa.bm = c->wplan.bm;
+        wa.part = c->part_w;
+        wa.part_stride = (int64_t)c->cmax * c->cmax;
+        wa.gsum = c->gsum_w;
+        wa.counters = c->counters_w;
+        wa.vec = 1;
+        wa.out = c->GW;
+        POD_TRY(launch_tall<T>(TALL_PROJ, wa, c->wplan, s));
+        mark(c);
+        RowsSmallArgs rs{};
+        rs.st = c->st;
+        rs.stc = c->aux + 5;
+        rs.dtype = c->p.dtype;
+        rs.r = c->rmax;
+        rs.rmax = c->rmax;
+        rs.cmax = c->cmax;
+        rs.GW = c->GW;
+        rs.Ym = c->rYm;
+        POD_TRY(launch_rows_small(rs, s));
+        mark(c);
+        TallArgs<T> ca = tall_args<T>(c, c->part, 0);
+        ca.st = c->aux + 5;
+        ca.U = (T *)c->Cbuf;
+        ca.Ym = c->rYm;
+        POD_TRY(launch_tall<T>(TALL_UPDATE, ca, c->plan, s));
+        mark(c);
+        ta.A = (const T *)c->Cbuf;
+        ta.idx = nullptr;
+        ta.lda = c->p.m;
+        ta.vec = (c->p.m * (int64_t)sizeof(T)) % 16 == 0;
+    }
     ta.out = c->P;
     POD_TRY(launch_tall<T>(TALL_PROJ, ta, c->plan, s));
     mark(c);
@@ -489,6 +592,16 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         const size_t esz = p->dtype == POD_F32 ? 4 : 8;
         c->vec = ((uintptr_t)A_dev % 16 == 0) && ((p->lda * esz) % 16 == 0) && ((p->m * esz) % 16 == 0);
     }
+    if (p->rows) {
+        c->wdraws = (int)(p->w > 0 ? (p->w < p->m ? p->w : p->m) : default_row_draws(p->k, p->m));
+        c->ldw = (c->wdraws + 3) & ~3;
+        c->rnb = row_blocks(p->m);
+        c->wplan = tall_plan(p->dtype, c->wdraws, c->cmax, c->cmax, c->sms);
+        if (rows_small_smem(c->cmax) > 220 * 1024 || c->wplan.smem > 227 * 1024) {
+            free(c);
+            return POD_EUNSUPPORTED;
+        }
+    }
     if (core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) > 220 * 1024 ||
         small_chol_smem(c->cmax) > 220 * 1024 || c->plan.smem > 227 * 1024) {
         free(c);
@@ -516,7 +629,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     ALLOC(c->hist_g, n + 1);
     ALLOC(c->hist_measure, n + 1);
     ALLOC(c->st, 1);
-    ALLOC(c->aux, 4);
+    ALLOC(c->aux, 6);
     ALLOC(c->part, (size_t)c->plan.grid * ((size_t)rm * cm + (size_t)cm * cm));
     ALLOC(c->part_atu, (size_t)c->aplan.split * n * rm);
     ALLOC(c->P, (size_t)rm * cm);
@@ -541,6 +654,31 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     ALLOC(c->dots, rm);
     c->sign_grid = 2 * c->sms;
     ALLOC(c->part_sign, (size_t)c->sign_grid * rm);
+    if (p->rows) {
+        const int nb = c->rnb;
+        ALLOC(c->r_val, m);
+        ALLOC(c->r_bmax, nb);
+        ALLOC(c->r_bsum, nb);
+        ALLOC(c->r_boff, nb);
+        ALLOC(c->r_total, 1);
+        ALLOC(c->r_w, m);
+        ALLOC(c->r_cdf, m);
+        ALLOC(c->r_cnt, m);
+        ALLOC(c->r_rows, c->wdraws);
+        ALLOC(c->r_rcnt, c->wdraws);
+        ALLOC(c->r_rscale, c->wdraws);
+        ALLOC(c->r_h, 1);
+        unsigned char *Wb = nullptr, *Cb = nullptr;
+        ALLOC(Wb, (size_t)c->ldw * cm * es);
+        ALLOC(Cb, (size_t)m * rm * es);
+        c->Wrows = Wb;
+        c->Cbuf = Cb;
+        ALLOC(c->GW, (size_t)cm * cm);
+        ALLOC(c->rYm, (size_t)cm * rm);
+        ALLOC(c->part_w, (size_t)c->wplan.grid * cm * cm);
+        ALLOC(c->gsum_w, (size_t)(c->wplan.groups + 1) * cm * cm);
+        ALLOC(c->counters_w, 64 + c->wplan.groups);
+    }
 #undef ALLOC
     if (st == POD_OK && cudaMallocHost((void **)&c->hstate, sizeof(DevState)) != cudaSuccess) {
         cudaGetLastError();
@@ -563,6 +701,12 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_g, 0, (n + 1) * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, (64 + c->plan.groups) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->atu_counters, 0, (c->aplan.grid.x + 64) * sizeof(unsigned), s);
+    if (p->rows) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->r_cnt, 0, (size_t)m * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->r_h, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->counters_w, 0, (64 + c->wplan.groups) * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->part_w, 0, (size_t)c->wplan.grid * cm * cm * 8, s);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         ctx_free(c);
@@ -701,6 +845,29 @@ pod_status pod_backward(pod_ctx *c, const void *dU_dev, const double *dsigma_dev
     return POD_EUNSUPPORTED;
 }
 
+pod_status pod_last_rows(pod_ctx *c, int32_t *rows_host, int32_t *counts_host, int32_t cap, int32_t *h) {
+    if (!c || !h) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (!c->p.rows) return POD_ESTATE;
+    int32_t hh = 0;
+    POD_CUDA_TRY(cudaMemcpyAsync(&hh, c->r_h, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    POD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *h = hh;
+    if (hh > cap) return POD_EINVAL;
+    if (hh > 0 && rows_host)
+        POD_CUDA_TRY(cudaMemcpyAsync(rows_host, c->r_rows, (size_t)hh * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (hh > 0 && counts_host)
+        POD_CUDA_TRY(cudaMemcpyAsync(counts_host, c->r_rcnt, (size_t)hh * 4, cudaMemcpyDeviceToHost, c->stream));
+    POD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return POD_OK;
+}
+
+pod_status pod_row_draws(pod_ctx *c, int32_t *w) {
+    if (!c || !w) return POD_EINVAL;
+    *w = c->p.rows ? c->wdraws : 0;
+    return POD_OK;
+}
+
 static pod_status reset_state(pod_ctx *c) {
     cudaStream_t s = c->stream;
     const size_t es = c->p.dtype == POD_F32 ? 4 : 8;
@@ -710,6 +877,7 @@ static pod_status reset_state(pod_ctx *c) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->mask, 1, n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ort, 0, n * sizeof(double), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_g, 0, (n + 1) * sizeof(int32_t), s);
+    if (e == cudaSuccess && c->p.rows) e = cudaMemsetAsync(c->r_h, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return POD_ECUDA;

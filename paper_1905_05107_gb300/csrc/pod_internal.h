@@ -112,6 +112,42 @@ template <typename T>
 pod_status launch_sign_dots(const T *U, int64_t m, int64_t ldu, int r, uint64_t seed,
                             double *part, int grid, cudaStream_t st);
 
+// ------------------------------------------------------------------- rows.cu
+// Row sampling of ICRS (Algorithm 1, SAMPLE AND SCALE UNIQUE ROWS).
+template <typename T>
+struct RowArgs {
+    int64_t m;
+    const T *A;
+    int64_t lda;
+    const int32_t *idx;     // sampled columns (g = st->g of them)
+    const T *U;             // current modes (leverage scores)
+    int64_t ldu;
+    const DevState *st;
+    int k;
+    int row_strategy;
+    int L;                  // weight bits for m rows
+    int nblocks;            // ceil(m / 1024)
+    int wdraws;             // row draws w
+    int ldw;                // leading dimension of W (>= wdraws, multiple of 4)
+    int cmax;
+    uint64_t seed;
+    DevState *stw;          // state of the pass G_W = W^T W (written here)
+    double *val;            // m row values
+    double *bmax;           // nblocks
+    uint64_t *w;            // m integer weights
+    unsigned long long *bsum, *boff;   // nblocks
+    unsigned long long *total;         // 1
+    uint64_t *cdf;          // m
+    unsigned *cnt;          // m, zero between rounds
+    int32_t *rows, *rcnt;   // wdraws
+    double *rscale;         // wdraws
+    int32_t *h;             // distinct rows
+    T *W;                   // ldw x cmax
+};
+template <typename T>
+pod_status launch_rows(const RowArgs<T> &a, cudaStream_t s, int sms);
+int row_blocks(int64_t m);
+
 // ------------------------------------------------------------------ small.cu
 pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t count,
                          double *out, const DevState *st, cudaStream_t s);
@@ -155,4 +191,16 @@ struct RefineArgs {
     double *K;              // out: r x r (ld r), V <- Y K
 };
 pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s);
+
+// ICRS: right vectors of W from G_W = W^T W (g x g, ld cmax): V_r (g x rc,
+// written to Ym with ld rmax), rc = min(r, g); sets stc = {r_cur 0, g,
+// r_new rc} for the pass C = D V_r, then the round's block width st->g = rc.
+struct RowsSmallArgs {
+    DevState *st, *stc;
+    int dtype, r, rmax, cmax;
+    const double *GW;
+    double *Ym;
+};
+pod_status launch_rows_small(const RowsSmallArgs &a, cudaStream_t s);
+size_t rows_small_smem(int cmax);
 pod_status launch_refine_svd(const RefineArgs &a, cudaStream_t s);

@@ -1019,6 +1019,81 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// ICRS (Algorithm 1, GET UPDATE with rows): the top right singular vectors
+// V_r of the scaled row block W from its Gram G_W = W^T W (g x g, FP64,
+// ld cmax).  G_W = R^T R (Cholesky with dropped dependent pivots), then
+// one-sided Jacobi on the columns of R: R V = B, so V diagonalises G_W and
+// the column norms of B are the singular values of W.  V_r = the columns of
+// V for the rc = min(r, g) largest, written as the coefficient block of the
+// pass C = D V_r (Ym[j * rmax + s]).  The state of that pass is stc =
+// {r_cur 0, g, r_new rc}; the round's block width becomes rc.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SMALL_THREADS) k_rows_small(RowsSmallArgs a) {
+    DevState *st = a.st;
+    const int g = st->g, done = st->done, t = st->t;
+    const int rc = g < a.r ? g : a.r;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    if (tid == 0) {
+        DevState s{};
+        s.done = done;
+        s.t = t;
+        s.r_cur = 0;
+        s.g = g;
+        s.r_new = rc;
+        *a.stc = s;
+    }
+    if (done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Carve cv{smem_raw};
+    double *W = cv.take<double>((size_t)g * g);
+    double *R = cv.take<double>((size_t)g * g);
+    double *V = cv.take<double>((size_t)g * g);
+    double *alpha = cv.take<double>(g);
+    int *order = cv.take<int>(g);
+    __shared__ int s_flag[2];
+    __shared__ double red[32];
+    __shared__ double piv3[3];
+    if (tid == 0) s_flag[1] = 0;
+    double dmax = 0.0;
+    for (int j = tid; j < g; j += bd) dmax = a.GW[j * a.cmax + j] > dmax ? a.GW[j * a.cmax + j] : dmax;
+    dmax = block_max<double>(dmax, red);
+    for (int e = tid; e < g * g; e += bd) {
+        const int i = e / g, j = e % g;
+        W[e] = i <= j ? a.GW[i * a.cmax + j] : 0.0;
+    }
+    __syncthreads();
+    const double eps = g * 1.1102230246251565e-16;
+    chol_drop<double>(W, g, g, eps * eps * dmax, R, g, piv3);
+    for (int e = tid; e < g * g; e += bd) {
+        const int q = e / g, p = e % g;   // W <- B, column-major: column q of R
+        W[q * g + p] = R[p * g + q];
+        V[q * g + p] = (p == q) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    jacobi_hw<double>(W, g, g, g, V, g, alpha, 2.0 * sqrt((double)g) * 2.220446049250313e-16, 40, s_flag);
+    sort_desc<double>(alpha, g, order);
+    for (int e = tid; e < g * rc; e += bd) {
+        const int j = e / rc, s = e % rc;
+        a.Ym[j * a.rmax + s] = V[order[s] * g + j];
+    }
+    __syncthreads();
+    if (tid == 0) st->g = rc;
+}
+
+size_t rows_small_smem(int cmax) {
+    return 3 * al16x((size_t)cmax * cmax * 8) + al16x((size_t)cmax * 8) + al16x((size_t)cmax * 4) + 64;
+}
+
+pod_status launch_rows_small(const RowsSmallArgs &a, cudaStream_t s) {
+    const size_t smem = rows_small_smem(a.cmax);
+    if (smem > 220 * 1024) return POD_EUNSUPPORTED;
+    POD_CUDA_TRY(cudaFuncSetAttribute(k_rows_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rows_small<<<1, SMALL_THREADS, smem, s>>>(a);
+    POD_CUDA_TRY(cudaGetLastError());
+    return POD_OK;
+}
+
 pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s) {
     const size_t smem = 4 * al16x((size_t)a.r * a.r * 8) + 64;
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;

@@ -29,10 +29,11 @@ POD_CORE_AUTO, POD_CORE_F32, POD_CORE_F64 = 0, 1, 2
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
             "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
-            "pod_sample_noalloc"]
+            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws"]
 
 ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "core_svd", "update", "finish"]
 ORT_KERNELS = ["ort_atu", "ort_values"]
+ROW_KERNELS = ["rows_sample", "rows_gram", "rows_svd", "rows_block"]
 
 
 class PodParams(ctypes.Structure):
@@ -129,6 +130,7 @@ def _check_colmajor(A):
 _STRATEGY = {"l2n": POD_L2N, "unf": POD_UNF, "ort": POD_ORT}
 _CRITERION = {"subspace": POD_SUBSPACE, "modes": POD_MODES}
 _CORE = {"auto": POD_CORE_AUTO, "f32": POD_CORE_F32, "f64": POD_CORE_F64}
+_ROW_STRATEGY = {"l2n": POD_ROW_L2N, "ls": POD_ROW_LS}
 
 
 @dataclass
@@ -146,7 +148,8 @@ class Context:
 
     def __init__(self, A, k: int, c: int, r: int = 0, col_strategy: str = "unf",
                  criterion: str = "subspace", tol: float = 1e-8, max_iter: int = 0,
-                 refine: bool = True, seed: int = 0x5107, core: str = "auto", stream=None):
+                 refine: bool = True, seed: int = 0x5107, core: str = "auto", rows: bool = False,
+                 row_strategy: str = "l2n", w: int = 0, stream=None):
         import torch
         _check_colmajor(A)
         self.A = A                    # keeps the borrowed buffer alive
@@ -158,10 +161,10 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(A.device)
         p = PodParams()
         p.m, p.n, p.lda = self.m, self.n, int(A.stride(1))
-        p.k, p.c, p.w, p.r = int(k), int(c), 0, int(r)
-        p.rows = 0
+        p.k, p.c, p.w, p.r = int(k), int(c), int(w), int(r)
+        p.rows = 1 if rows else 0
         p.col_strategy = _STRATEGY[col_strategy]
-        p.row_strategy = POD_ROW_L2N
+        p.row_strategy = _ROW_STRATEGY[row_strategy]
         p.criterion = _CRITERION[criterion]
         p.tol = float(tol)
         p.max_iter = int(max_iter)
@@ -223,7 +226,8 @@ class Context:
         buf = (ctypes.c_float * 32)()
         cnt = ctypes.c_int32(0)
         _check(lib().pod_round_timings(self._h, buf, 32, ctypes.byref(cnt)), "pod_round_timings")
-        names = (ORT_KERNELS if self.params.col_strategy == POD_ORT else []) + ROUND_KERNELS
+        names = (ORT_KERNELS if self.params.col_strategy == POD_ORT else []) + ROUND_KERNELS[:1] + \
+            (ROW_KERNELS if self.params.rows else []) + ROUND_KERNELS[1:]
         return dict(zip(names, [float(x) for x in buf[: cnt.value]]))
 
     def counters(self):
@@ -245,6 +249,21 @@ class Context:
         meas = ctypes.c_double(0.0)
         _check(lib().pod_get_trace(self._h, int(t), idx, ctypes.byref(g), ctypes.byref(meas)), "pod_get_trace")
         return np.array(idx[: g.value], dtype=np.int64), float(meas.value)
+
+    def row_draws(self) -> int:
+        """w, the row draws per ICRS iteration (0 without rows)."""
+        w = ctypes.c_int32(0)
+        _check(lib().pod_row_draws(self._h, ctypes.byref(w)), "pod_row_draws")
+        return int(w.value)
+
+    def last_rows(self):
+        """(distinct rows ascending, their draw counts) of the latest ICRS round."""
+        cap = max(1, self.row_draws())
+        rows = (ctypes.c_int32 * cap)()
+        cnt = (ctypes.c_int32 * cap)()
+        h = ctypes.c_int32(0)
+        _check(lib().pod_last_rows(self._h, rows, cnt, cap, ctypes.byref(h)), "pod_last_rows")
+        return np.array(rows[: h.value], dtype=np.int64), np.array(cnt[: h.value], dtype=np.int64)
 
     def replay(self, index_sets: List[np.ndarray]):
         flat = np.concatenate([np.asarray(s, dtype=np.int32) for s in index_sets]) if index_sets else \
