@@ -16,7 +16,7 @@
 
 namespace {
 
-constexpr int ROW_KERNELS = 9;   // launches of launch_rows
+constexpr int ROW_KERNELS = 8;   // launches of launch_rows
 
 template <typename T>
 __global__ void k_write_modes(const T *U, int64_t m, int r_cur, int k, const double *sigma,
@@ -109,16 +109,16 @@ struct pod_ctx {
     double *rG, *rG2, *rM1, *rR1p, *rsig, *rVR, *rK, *dots, *part_sign;
     int32_t *replay_idx, *replay_off;
     int replay_T;
-    // ICRS (rows = 1): row sampling buffers, the scaled row block W (ldw x
-    // cmax), its Gram G_W, the coefficients V_r and the new block C = D V_r
-    int wdraws, ldw, rnb;
-    TallPlan wplan;
+    // ICRS (rows = 1): row sampling buffers, the Gram G_W of the scaled row
+    // block, the coefficients V_r and the new block C = D V_r
+    int wdraws, rnb;
+    RowGramPlan gplan;
     double *r_val, *r_bmax, *r_rscale, *GW, *rYm, *part_w, *gsum_w;
     unsigned long long *r_bsum, *r_boff, *r_total;
     uint64_t *r_w, *r_cdf;
     unsigned *r_cnt, *counters_w;
     int32_t *r_rows, *r_rcnt, *r_h;
-    void *Wrows, *Cbuf;
+    void *Cbuf;
     // host
     DevState *hstate;   // pinned mirror
     cudaGraphExec_t graph;
@@ -149,7 +149,7 @@ static void ctx_free(pod_ctx *c) {
                     c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
-                    c->r_rcnt, c->r_h, c->Wrows, c->Cbuf};
+                    c->r_rcnt, c->r_h, c->Cbuf};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->hstate) cudaFreeHost(c->hstate);
@@ -308,10 +308,8 @@ static pod_status enqueue_round(pod_ctx *c) {
         ra.L = weight_bits(c->p.m);
         ra.nblocks = c->rnb;
         ra.wdraws = c->wdraws;
-        ra.ldw = c->ldw;
         ra.cmax = c->cmax;
         ra.seed = c->p.seed;
-        ra.stw = c->aux + 4;
         ra.val = c->r_val;
         ra.bmax = c->r_bmax;
         ra.w = c->r_w;
@@ -324,28 +322,17 @@ static pod_status enqueue_round(pod_ctx *c) {
         ra.rcnt = c->r_rcnt;
         ra.rscale = c->r_rscale;
         ra.h = c->r_h;
-        ra.W = (T *)c->Wrows;
+        ra.ggrid = c->gplan.grid;
+        ra.rows_per = c->gplan.rows_per;
+        ra.lds = c->gplan.lds;
+        ra.part = c->part_w;
+        ra.gsum = c->gsum_w;
+        ra.gcounters = c->counters_w;
+        ra.GW = c->GW;
         POD_TRY(launch_rows<T>(ra, s, c->sms));
         c->launches += ROW_KERNELS - 1;
         mark(c);
-        TallArgs<T> wa{};
-        wa.m = c->wdraws;
-        wa.A = (const T *)c->Wrows;
-        wa.lda = c->ldw;
-        wa.idx = nullptr;
-        wa.U = (T *)c->Wrows;
-        wa.ldu = c->ldw;
-        wa.st = c->aux + 4;
-        wa.rmax = c->cmax;
-        wa.cmax = c->cmax;
-        wa.bm = c->wplan.bm;
-        wa.part = c->part_w;
-        wa.part_stride = (int64_t)c->cmax * c->cmax;
-        wa.gsum = c->gsum_w;
-        wa.counters = c->counters_w;
-        wa.vec = 1;
-        wa.out = c->GW;
-        POD_TRY(launch_tall<T>(TALL_PROJ, wa, c->wplan, s));
+        POD_TRY(launch_row_gram<T>(ra, s));
         mark(c);
         RowsSmallArgs rs{};
         rs.st = c->st;
@@ -593,11 +580,10 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         c->vec = ((uintptr_t)A_dev % 16 == 0) && ((p->lda * esz) % 16 == 0) && ((p->m * esz) % 16 == 0);
     }
     if (p->rows) {
-        c->wdraws = (int)(p->w > 0 ? (p->w < p->m ? p->w : p->m) : default_row_draws(p->k, p->m));
-        c->ldw = (c->wdraws + 3) & ~3;
+        c->wdraws = (int)(p->w > 0 ? p->w : default_row_draws(p->k, p->m));   // draws with replacement: w may exceed m
         c->rnb = row_blocks(p->m);
-        c->wplan = tall_plan(p->dtype, c->wdraws, c->cmax, c->cmax, c->sms);
-        if (rows_small_smem(c->cmax) > 220 * 1024 || c->wplan.smem > 227 * 1024) {
+        c->gplan = row_gram_plan(p->dtype, c->wdraws, c->cmax, c->sms);
+        if (rows_small_smem(c->cmax) > 220 * 1024) {
             free(c);
             return POD_EUNSUPPORTED;
         }
@@ -668,16 +654,14 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         ALLOC(c->r_rcnt, c->wdraws);
         ALLOC(c->r_rscale, c->wdraws);
         ALLOC(c->r_h, 1);
-        unsigned char *Wb = nullptr, *Cb = nullptr;
-        ALLOC(Wb, (size_t)c->ldw * cm * es);
+        unsigned char *Cb = nullptr;
         ALLOC(Cb, (size_t)m * rm * es);
-        c->Wrows = Wb;
         c->Cbuf = Cb;
         ALLOC(c->GW, (size_t)cm * cm);
         ALLOC(c->rYm, (size_t)cm * rm);
-        ALLOC(c->part_w, (size_t)c->wplan.grid * cm * cm);
-        ALLOC(c->gsum_w, (size_t)(c->wplan.groups + 1) * cm * cm);
-        ALLOC(c->counters_w, 64 + c->wplan.groups);
+        ALLOC(c->part_w, (size_t)c->gplan.grid * cm * cm);
+        ALLOC(c->gsum_w, (size_t)(c->gplan.groups + 1) * cm * cm);
+        ALLOC(c->counters_w, c->gplan.groups + 1);
     }
 #undef ALLOC
     if (st == POD_OK && cudaMallocHost((void **)&c->hstate, sizeof(DevState)) != cudaSuccess) {
@@ -704,8 +688,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (p->rows) {
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_cnt, 0, (size_t)m * sizeof(unsigned), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_h, 0, sizeof(int32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->counters_w, 0, (64 + c->wplan.groups) * sizeof(unsigned), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->part_w, 0, (size_t)c->wplan.grid * cm * cm * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->counters_w, 0, (c->gplan.groups + 1) * sizeof(unsigned), s);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

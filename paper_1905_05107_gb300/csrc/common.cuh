@@ -230,3 +230,45 @@ __device__ __forceinline__ dfloat x_shfl_xor(dfloat v, int o) {
     } while (0)
 
 static inline int pod_ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// CTAs per first-level group of the in-kernel partial sums (tall_reduce)
+constexpr int RED_GROUP = 16;
+
+// Sum of FP64 partials inside the kernel: the last CTA to arrive in each
+// group of RED_GROUP CTAs sums that group's partials; the last group to
+// finish sums the group results.  Orders are fixed by block index; arrival
+// counters are reset by the CTAs that consumed them.
+__device__ inline void tall_reduce(const double *part, double *gsum, double *out, int count, int64_t stride,
+                            unsigned *counters, int *s_flag) {
+    const int tid = threadIdx.x;
+    const int grid = gridDim.x;
+    const int ngroups = (grid + RED_GROUP - 1) / RED_GROUP;
+    const int grp = blockIdx.x / RED_GROUP;
+    const int gsize = min(RED_GROUP, grid - grp * RED_GROUP);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *s_flag = (atomicAdd(&counters[grp], 1u) == (unsigned)(gsize - 1));
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    for (int e = tid; e < count; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < gsize; ++b) s += __ldcg(part + (int64_t)(grp * RED_GROUP + b) * stride + e);
+        gsum[(int64_t)grp * stride + e] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        counters[grp] = 0;
+        *s_flag = (atomicAdd(&counters[ngroups], 1u) == (unsigned)(ngroups - 1));
+    }
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    for (int e = tid; e < count; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < ngroups; ++b) s += __ldcg(gsum + (int64_t)b * stride + e);
+        out[e] = s;
+    }
+    if (tid == 0) counters[ngroups] = 0;
+}

@@ -113,7 +113,8 @@ pod_status launch_sign_dots(const T *U, int64_t m, int64_t ldu, int r, uint64_t 
                             double *part, int grid, cudaStream_t st);
 
 // ------------------------------------------------------------------- rows.cu
-// Row sampling of ICRS (Algorithm 1, SAMPLE AND SCALE UNIQUE ROWS).
+// Row sampling of ICRS (Algorithm 1, SAMPLE AND SCALE UNIQUE ROWS) and the
+// Gram G_W = W^T W of the scaled row block.
 template <typename T>
 struct RowArgs {
     int64_t m;
@@ -128,10 +129,8 @@ struct RowArgs {
     int L;                  // weight bits for m rows
     int nblocks;            // ceil(m / 1024)
     int wdraws;             // row draws w
-    int ldw;                // leading dimension of W (>= wdraws, multiple of 4)
     int cmax;
     uint64_t seed;
-    DevState *stw;          // state of the pass G_W = W^T W (written here)
     double *val;            // m row values
     double *bmax;           // nblocks
     uint64_t *w;            // m integer weights
@@ -142,10 +141,21 @@ struct RowArgs {
     int32_t *rows, *rcnt;   // wdraws
     double *rscale;         // wdraws
     int32_t *h;             // distinct rows
-    T *W;                   // ldw x cmax
+    // Gram pass: ggrid CTAs of rows_per rows (shared column stride lds)
+    int ggrid, rows_per, lds;
+    double *part;           // ggrid x cmax^2
+    double *gsum;           // (groups + 1) x cmax^2
+    unsigned *gcounters;    // groups + 1, zero between launches
+    double *GW;             // cmax x cmax, upper triangle
 };
+struct RowGramPlan {
+    int grid, rows_per, lds, groups;
+};
+RowGramPlan row_gram_plan(int dtype, int wdraws, int cmax, int sms);
 template <typename T>
 pod_status launch_rows(const RowArgs<T> &a, cudaStream_t s, int sms);
+template <typename T>
+pod_status launch_row_gram(const RowArgs<T> &a, cudaStream_t s);
 int row_blocks(int64_t m);
 
 // ------------------------------------------------------------------ small.cu

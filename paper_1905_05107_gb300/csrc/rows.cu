@@ -8,8 +8,8 @@
 //   scaled by sqrt(t_hat_l W / (w w_{I_r[l]}))  (q = w_i / W is the quantised
 //   probability actually used).
 // The m-length passes run on the whole GPU (block partials plus one-block
-// scans of the partials); the right vectors of W come from the small
-// kernel k_rows_small.
+// scans of the partials); W^T W is formed straight from the gathered rows
+// (k_row_gram) and its eigenvectors come from the small kernel k_rows_small.
 #include "pod_internal.h"
 
 namespace {
@@ -210,30 +210,55 @@ __global__ void __launch_bounds__(RB) k_row_compact(RowArgs<T> a) {
     }
 }
 
-// W (ldw x g, column-major): scaled distinct rows, zero beyond h; the state
-// of the Gram pass over W is {r_cur = g, g}
+// G_W = W^T W without materialising W: each CTA gathers its share of the h
+// scaled rows (row l of W = d^{I_r[l]} * scale_l) into shared memory and
+// forms its partial Gram; the partials are summed in a fixed order in FP64.
+// FP32 data: the eigenvectors of a Gram formed in FP32 lose accuracy as
+// sigma_1^2 / (sigma_r^2 - sigma_{r+1}^2), so every product is split exactly
+// (TwoProduct) and summed with TwoSum into a (hi, lo) pair; FP64 data uses
+// FP64 FMAs.  Upper triangle, ld cmax.
 template <typename T>
-__global__ void k_row_build_w(RowArgs<T> a) {
+__global__ void __launch_bounds__(256) k_row_gram(RowArgs<T> a) {
     const DevState *st = a.st;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        DevState s{};
-        s.done = st->done;
-        s.t = st->t;
-        s.r_cur = st->g;
-        s.g = st->g;
-        *a.stw = s;
-    }
     if (st->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ws = reinterpret_cast<T *>(smem_raw);   // column j at j * lds
+    __shared__ int s_flag;
     const int g = st->g, h = a.h[0];
-    const int64_t total = (int64_t)a.ldw * g;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / a.ldw);
-        const int l = (int)(e - (int64_t)j * a.ldw);
-        T v = (T)0;
-        if (l < h) v = (T)((double)a.A[(int64_t)a.idx[j] * a.lda + a.rows[l]] * a.rscale[l]);
-        a.W[(int64_t)j * a.ldw + l] = v;
+    const int rp = a.rows_per, lds = a.lds;
+    const int r0 = blockIdx.x * rp;
+    const int nr = max(0, min(rp, h - r0));
+    for (int e = threadIdx.x; e < nr * g; e += blockDim.x) {
+        const int j = e / nr, l = e - j * nr;
+        Ws[j * lds + l] = (T)((double)a.A[(int64_t)a.idx[j] * a.lda + a.rows[r0 + l]] * a.rscale[r0 + l]);
     }
+    __syncthreads();
+    const int cm = a.cmax;
+    double *out = a.part + (int64_t)blockIdx.x * cm * cm;
+    for (int e = threadIdx.x; e < g * cm; e += blockDim.x) {
+        const int p = e / cm, q = e - p * cm;
+        double v = 0.0;
+        if (q >= p && q < g) {
+            const T *x = Ws + p * lds, *y = Ws + q * lds;
+            if constexpr (sizeof(T) == 4) {
+                dfloat acc{0.f, 0.f};
+                for (int l = 0; l < nr; ++l) {
+                    const float pr = x[l] * y[l];
+                    const float er = fmaf(x[l], y[l], -pr);
+                    const dfloat s = df_two_sum(acc.hi, pr);
+                    acc.hi = s.hi;
+                    acc.lo += s.lo + er;
+                }
+                v = (double)acc.hi + (double)acc.lo;
+            } else {
+                double acc = 0.0;
+                for (int l = 0; l < nr; ++l) acc = fma(x[l], y[l], acc);
+                v = acc;
+            }
+        }
+        out[e] = v;
+    }
+    tall_reduce(a.part, a.gsum, a.GW, g * cm, (int64_t)cm * cm, a.gcounters, &s_flag);
 }
 
 }  // namespace
@@ -252,15 +277,37 @@ pod_status launch_rows(const RowArgs<T> &a, cudaStream_t s, int sms) {
     k_row_nzcount<T><<<nb, RB, 0, s>>>(a);
     k_row_offsets<T><<<1, RB, 0, s>>>(a, 0);
     k_row_compact<T><<<nb, RB, 0, s>>>(a);
-    int bg = (int)(((int64_t)a.ldw * a.cmax + 255) / 256);
-    if (bg > 8 * sms) bg = 8 * sms;
-    if (bg < 1) bg = 1;
-    k_row_build_w<T><<<bg, 256, 0, s>>>(a);
+    POD_CUDA_TRY(cudaGetLastError());
+    return POD_OK;
+}
+
+template <typename T>
+pod_status launch_row_gram(const RowArgs<T> &a, cudaStream_t s) {
+    const size_t smem = (size_t)a.lds * a.cmax * sizeof(T);
+    POD_CUDA_TRY(cudaFuncSetAttribute(k_row_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_row_gram<T><<<a.ggrid, 256, smem, s>>>(a);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }
 
 int row_blocks(int64_t m) { return (int)((m + RB - 1) / RB); }
 
+RowGramPlan row_gram_plan(int dtype, int wdraws, int cmax, int sms) {
+    RowGramPlan p{};
+    const size_t es = dtype == POD_F32 ? 4 : 8;
+    const int max_rows = (int)((96 * 1024) / ((size_t)cmax * es)) - 1;   // shared-memory cap per CTA
+    int grid = 2 * sms;
+    if ((wdraws + grid - 1) / grid > max_rows) grid = (wdraws + max_rows - 1) / max_rows;
+    if (grid > (wdraws + 15) / 16) grid = (wdraws + 15) / 16;
+    if (grid < 1) grid = 1;
+    p.grid = grid;
+    p.rows_per = (wdraws + grid - 1) / grid;
+    p.lds = p.rows_per | 1;   // odd column stride: conflict-free shared loads across columns
+    p.groups = (grid + RED_GROUP - 1) / RED_GROUP;
+    return p;
+}
+
 template pod_status launch_rows<float>(const RowArgs<float> &, cudaStream_t, int);
 template pod_status launch_rows<double>(const RowArgs<double> &, cudaStream_t, int);
+template pod_status launch_row_gram<float>(const RowArgs<float> &, cudaStream_t);
+template pod_status launch_row_gram<double>(const RowArgs<double> &, cudaStream_t);

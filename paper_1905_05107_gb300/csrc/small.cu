@@ -1029,7 +1029,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
 // pass C = D V_r (Ym[j * rmax + s]).  The state of that pass is stc =
 // {r_cur 0, g, r_new rc}; the round's block width becomes rc.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SMALL_THREADS) k_rows_small(RowsSmallArgs a) {
+__global__ void __launch_bounds__(CORE_THREADS) k_rows_small(RowsSmallArgs a) {
     DevState *st = a.st;
     const int g = st->g, done = st->done, t = st->t;
     const int rc = g < a.r ? g : a.r;
@@ -1089,7 +1089,7 @@ pod_status launch_rows_small(const RowsSmallArgs &a, cudaStream_t s) {
     const size_t smem = rows_small_smem(a.cmax);
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     POD_CUDA_TRY(cudaFuncSetAttribute(k_rows_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_rows_small<<<1, SMALL_THREADS, smem, s>>>(a);
+    k_rows_small<<<1, CORE_THREADS, smem, s>>>(a);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }

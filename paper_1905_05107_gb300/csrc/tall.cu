@@ -23,7 +23,6 @@
 namespace {
 
 constexpr int TALL_THREADS = 256;
-constexpr int RED_GROUP = 16;
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
@@ -211,45 +210,6 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
         }
         store(rc, cj, a1, a2);
     }
-}
-
-// Sum of FP64 partials inside the kernel: the last CTA to arrive in each
-// group of RED_GROUP CTAs sums that group's partials; the last group to
-// finish sums the group results.  Orders are fixed by block index; arrival
-// counters are reset by the CTAs that consumed them.
-__device__ void tall_reduce(const double *part, double *gsum, double *out, int count, int64_t stride,
-                            unsigned *counters, int *s_flag) {
-    const int tid = threadIdx.x;
-    const int grid = gridDim.x;
-    const int ngroups = (grid + RED_GROUP - 1) / RED_GROUP;
-    const int grp = blockIdx.x / RED_GROUP;
-    const int gsize = min(RED_GROUP, grid - grp * RED_GROUP);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) *s_flag = (atomicAdd(&counters[grp], 1u) == (unsigned)(gsize - 1));
-    __syncthreads();
-    if (!*s_flag) return;
-    __threadfence();
-    for (int e = tid; e < count; e += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < gsize; ++b) s += __ldcg(part + (int64_t)(grp * RED_GROUP + b) * stride + e);
-        gsum[(int64_t)grp * stride + e] = s;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        counters[grp] = 0;
-        *s_flag = (atomicAdd(&counters[ngroups], 1u) == (unsigned)(ngroups - 1));
-    }
-    __syncthreads();
-    if (!*s_flag) return;
-    __threadfence();
-    for (int e = tid; e < count; e += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < ngroups; ++b) s += __ldcg(gsum + (int64_t)b * stride + e);
-        out[e] = s;
-    }
-    if (tid == 0) counters[ngroups] = 0;
 }
 
 struct SmemPlan {
