@@ -76,7 +76,7 @@ typedef struct pod_params {
                               the new block is C = D V_r, V_r the top r right
                               singular vectors of the scaled row sample W of
                               D (GET UPDATE with rows, SAMPLE AND SCALE
-                              UNIQUE ROWS); needs c <= 96                    */
+                              UNIQUE ROWS)                                  */
     int32_t col_strategy;  /* POD_L2N | POD_UNF | POD_ORT                    */
     int32_t row_strategy;  /* POD_ROW_L2N | POD_ROW_LS                       */
     int32_t criterion;     /* POD_SUBSPACE | POD_MODES                       */

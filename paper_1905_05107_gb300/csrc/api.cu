@@ -114,6 +114,7 @@ struct pod_ctx {
     int wdraws, rnb;
     RowGramPlan gplan;
     double *r_val, *r_bmax, *r_rscale, *GW, *rYm, *part_w, *gsum_w;
+    double *wR1p, *wG2, *wM1, *wsig, *wX;
     unsigned long long *r_bsum, *r_boff, *r_total;
     uint64_t *r_w, *r_cdf;
     unsigned *r_cnt, *counters_w;
@@ -149,7 +150,7 @@ static void ctx_free(pod_ctx *c) {
                     c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
-                    c->r_rcnt, c->r_h, c->Cbuf};
+                    c->r_rcnt, c->r_h, c->Cbuf, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->hstate) cudaFreeHost(c->hstate);
@@ -338,18 +339,33 @@ static pod_status enqueue_round(pod_ctx *c) {
         rs.st = c->st;
         rs.stc = c->aux + 5;
         rs.dtype = c->p.dtype;
-        rs.r = c->rmax;
-        rs.rmax = c->rmax;
+        rs.core_f64 = c->core_f64;
         rs.cmax = c->cmax;
         rs.GW = c->GW;
-        rs.Ym = c->rYm;
-        POD_TRY(launch_rows_small(rs, s));
+        rs.R1p = c->wR1p;
+        rs.G2 = c->wG2;
+        rs.M1 = c->wM1;
+        POD_TRY(launch_rows_chol(rs, s));
+        mark(c);
+        SmallArgs sw = small_args(c);
+        sw.st = c->aux + 5;
+        sw.r = c->rmax;
+        sw.G2 = c->wG2;
+        sw.M1 = c->wM1;
+        sw.R1p = c->wR1p;
+        sw.sigma = c->wsig;
+        sw.Xm = c->wX;
+        sw.Ym = c->rYm;
+        sw.hist_measure = nullptr;
+        POD_TRY(launch_core(sw, s));
         mark(c);
         TallArgs<T> ca = tall_args<T>(c, c->part, 0);
         ca.st = c->aux + 5;
         ca.U = (T *)c->Cbuf;
         ca.Ym = c->rYm;
         POD_TRY(launch_tall<T>(TALL_UPDATE, ca, c->plan, s));
+        mark(c);
+        POD_TRY(launch_rows_setg(c->st, c->aux + 5, s));
         mark(c);
         ta.A = (const T *)c->Cbuf;
         ta.idx = nullptr;
@@ -659,6 +675,11 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         c->Cbuf = Cb;
         ALLOC(c->GW, (size_t)cm * cm);
         ALLOC(c->rYm, (size_t)cm * rm);
+        ALLOC(c->wR1p, (size_t)cm * cm);
+        ALLOC(c->wG2, (size_t)cm * cm);
+        ALLOC(c->wM1, (size_t)cm * cm);
+        ALLOC(c->wsig, rm);
+        ALLOC(c->wX, (size_t)rm * rm);
         ALLOC(c->part_w, (size_t)c->gplan.grid * cm * cm);
         ALLOC(c->gsum_w, (size_t)(c->gplan.groups + 1) * cm * cm);
         ALLOC(c->counters_w, c->gplan.groups + 1);

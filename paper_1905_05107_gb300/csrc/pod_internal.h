@@ -202,15 +202,17 @@ struct RefineArgs {
 };
 pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s);
 
-// ICRS: right vectors of W from G_W = W^T W (g x g, ld cmax): V_r (g x rc,
-// written to Ym with ld rmax), rc = min(r, g); sets stc = {r_cur 0, g,
-// r_new rc} for the pass C = D V_r, then the round's block width st->g = rc.
+// ICRS: from G_W = W^T W (g x g, ld cmax) the inputs of a core SVD whose
+// left singular vectors are the eigenvectors of G_W (R1p = R_hat with
+// G_W = R_hat R_hat^T, G2 = M1 = I) and its state stc = {r_cur 0, g};
+// afterwards k_rows_setg sets the round's block width to the kept count.
 struct RowsSmallArgs {
     DevState *st, *stc;
-    int dtype, r, rmax, cmax;
+    int dtype, core_f64, cmax;
     const double *GW;
-    double *Ym;
+    double *R1p, *G2, *M1;
 };
-pod_status launch_rows_small(const RowsSmallArgs &a, cudaStream_t s);
+pod_status launch_rows_chol(const RowsSmallArgs &a, cudaStream_t s);
+pod_status launch_rows_setg(DevState *st, const DevState *stc, cudaStream_t s);
 size_t rows_small_smem(int cmax);
 pod_status launch_refine_svd(const RefineArgs &a, cudaStream_t s);

@@ -133,21 +133,35 @@ __device__ void trmm_upper(const X *A, int lda, const X *B, int ldb, int n, X *C
 // ---------------------------------------------------------------------------
 // One-sided (Hestenes) Jacobi on the columns of B (nrow x ncol, column-major,
 // ld ldb) with the rotations accumulated into V (ncol x ncol, ld ldv; V must
-// hold I on entry).  Round-robin tournament ordering; each half-warp rotates
-// one column pair, so a round is ceil(ncol/2) disjoint pairs and one
-// barrier.  Squared column norms are kept in alpha and updated
+// hold I on entry).  Round-robin tournament ordering; a group of LP lanes
+// rotates one column pair (MAXE elements per lane), so a round is
+// ceil(ncol/2) disjoint pairs and one barrier.  Only the warps that hold
+// pairs take part: they synchronise on hardware barrier 1 and the function
+// returns at once on the other threads (the caller's next __syncthreads
+// joins them).  Squared column norms are kept in alpha and updated
 // analytically after each rotation (alpha_p - t g, alpha_q + t g), then
 // recomputed exactly at every sweep; only b_p . b_q is reduced per pair.
 // A pair is rotated while g^2 > tol^2 alpha_p alpha_q.  Bounded by
-// max_sweeps.  On return alpha holds exact squared norms.
+// max_sweeps.  On return alpha holds exact squared norms (on the working
+// threads; visible to all after the caller's barrier).
 // ---------------------------------------------------------------------------
-template <typename J, int MAXE>
-__device__ int jacobi_hw_n(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *alpha, J tol, int max_sweeps,
-                           int *s_flag) {
-    // MAXE elements per lane: nrow, ncol <= 16 * MAXE
-    const int tid = threadIdx.x, bd = blockDim.x;
-    const int lane = tid & 31, half = lane >> 4, l16 = lane & 15, warp = tid >> 5, nw = bd >> 5;
+__device__ __forceinline__ void bar_sync_1(int nthreads) {
+    asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
+}
+
+template <typename J, int LP, int MAXE>
+__device__ int jacobi_lp(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *alpha, J tol, int max_sweeps,
+                         int *s_flag) {
+    // nrow, ncol <= LP * MAXE
+    constexpr int PPW = 32 / LP;   // pairs per warp
     const int N = ncol + (ncol & 1), npairs = N / 2, M = N - 1;
+    int nwarps = (npairs + PPW - 1) / PPW;
+    if (nwarps > (int)(blockDim.x >> 5)) nwarps = blockDim.x >> 5;   // then warps take several pairs
+    if (nwarps < 1) nwarps = 1;
+    const int nwork = 32 * nwarps;
+    const int tid = threadIdx.x;
+    if (tid >= nwork) return 0;
+    const int lane = tid & 31, sub = lane / LP, lp = lane % LP, warp = tid >> 5;
     const J tol2 = tol * tol;
     // a sweep whose largest relative off-diagonal g^2 / (alpha_p alpha_q) stays
     // below loose2 leaves every pair below tol after its own rotations
@@ -155,113 +169,109 @@ __device__ int jacobi_hw_n(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *
     const J loose2 = (J)16 * tol;
     int sweep = 0;
     for (;; ++sweep) {
-        for (int c = tid; c < ncol; c += bd) {
+        for (int c = tid; c < ncol; c += nwork) {
             J s = 0;
             for (int i = 0; i < nrow; ++i) s = fma(B[(size_t)c * ldb + i], B[(size_t)c * ldb + i], s);
             alpha[c] = s;
         }
         if (tid == 0) *s_flag = 0;
-        __syncthreads();
+        bar_sync_1(nwork);
         if (sweep >= max_sweeps || ncol < 2) break;
         for (int rnd = 0; rnd < M; ++rnd) {
-            for (int base = 2 * warp; base < npairs; base += 2 * nw) {
-                const int pr = base + half;
-                int p = 0, q = 0;
-                bool valid = pr < npairs;
-                if (valid) {
-                    if (pr == 0) {
-                        p = M;
-                        q = rnd;
+          for (int pr0 = warp * PPW; pr0 < npairs; pr0 += nwork / LP) {
+            const int pr = pr0 + sub;
+            int p = 0, q = 0;
+            bool valid = pr < npairs;
+            if (valid) {
+                if (pr == 0) {
+                    p = M;
+                    q = rnd;
+                } else {
+                    p = rnd + pr;
+                    if (p >= M) p -= M;
+                    q = rnd - pr + M;
+                    if (q >= M) q -= M;
+                }
+                if (p >= ncol || q >= ncol) valid = false;
+                if (p > q) { int tmp = p; p = q; q = tmp; }
+            }
+            J *bp = B + (size_t)p * ldb, *bq = B + (size_t)q * ldb;
+            J *vp = V + (size_t)p * ldv, *vq = V + (size_t)q * ldv;
+            J x[MAXE], y[MAXE];
+            J g0 = 0, g1 = 0;
+#pragma unroll
+            for (int e = 0; e < MAXE; ++e) {
+                const int i = lp + LP * e;
+                const bool in = valid && i < nrow;
+                x[e] = in ? bp[i] : (J)0;
+                y[e] = in ? bq[i] : (J)0;
+                if (e & 1) g1 = fma(x[e], y[e], g1);
+                else g0 = fma(x[e], y[e], g0);
+            }
+            J g = g0 + g1;
+#pragma unroll
+            for (int o = LP / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, LP);
+            if (valid) {
+                const J a = alpha[p], b = alpha[q];
+                if (a > (J)0 && b > (J)0 && g * g > loose2 * loose2 * a * b && lp == 0) s_flag[1] = 1;
+                if (a > (J)0 && b > (J)0 && g * g > tol2 * a * b) {
+                    const J zeta = j_div(b - a, g + g);
+                    const J az = fabs(zeta);
+                    J t;
+                    if (az > (J)1e15) {
+                        t = j_div((J)0.5, zeta);
                     } else {
-                        p = rnd + pr;
-                        if (p >= M) p -= M;
-                        q = rnd - pr + M;
-                        if (q >= M) q -= M;
+                        const J w = (J)1 + zeta * zeta;
+                        t = j_div((J)1, az + w * j_rsqrt(w));
+                        if (zeta < (J)0) t = -t;
                     }
-                    if (p >= ncol || q >= ncol) valid = false;
-                    if (p > q) { int tmp = p; p = q; q = tmp; }
-                }
-                J *bp = B + (size_t)p * ldb, *bq = B + (size_t)q * ldb;
-                J *vp = V + (size_t)p * ldv, *vq = V + (size_t)q * ldv;
-                J x[MAXE], y[MAXE], vx[MAXE], vy[MAXE];
-                J g = 0;
+                    const J cs = j_rsqrt((J)1 + t * t), sn = cs * t;
 #pragma unroll
-                for (int e = 0; e < MAXE; ++e) {
-                    const int i = l16 + 16 * e;
-                    const bool in = valid && i < nrow;
-                    x[e] = in ? bp[i] : (J)0;
-                    y[e] = in ? bq[i] : (J)0;
-                    g = fma(x[e], y[e], g);
-                }
-#pragma unroll
-                for (int e = 0; e < MAXE; ++e) {
-                    const int i = l16 + 16 * e;
-                    const bool in = valid && i < ncol;
-                    vx[e] = in ? vp[i] : (J)0;
-                    vy[e] = in ? vq[i] : (J)0;
-                }
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, 16);
-                if (valid) {
-                    const J a = alpha[p], b = alpha[q];
-                    if (a > (J)0 && b > (J)0 && g * g > loose2 * loose2 * a * b && l16 == 0) s_flag[1] = 1;
-                    if (a > (J)0 && b > (J)0 && g * g > tol2 * a * b) {
-                        const J zeta = j_div(b - a, g + g);
-                        const J az = fabs(zeta);
-                        J t;
-                        if (az > (J)1e15) {
-                            t = j_div((J)0.5, zeta);
-                        } else {
-                            const J w = (J)1 + zeta * zeta;
-                            t = j_div((J)1, az + w * j_rsqrt(w));
-                            if (zeta < (J)0) t = -t;
+                    for (int e = 0; e < MAXE; ++e) {
+                        const int i = lp + LP * e;
+                        if (i < nrow) {
+                            bp[i] = cs * x[e] - sn * y[e];
+                            bq[i] = sn * x[e] + cs * y[e];
                         }
-                        const J cs = j_rsqrt((J)1 + t * t), sn = cs * t;
-#pragma unroll
-                        for (int e = 0; e < MAXE; ++e) {
-                            const int i = l16 + 16 * e;
-                            if (i < nrow) {
-                                bp[i] = cs * x[e] - sn * y[e];
-                                bq[i] = sn * x[e] + cs * y[e];
-                            }
-                            if (i < ncol) {
-                                vp[i] = cs * vx[e] - sn * vy[e];
-                                vq[i] = sn * vx[e] + cs * vy[e];
-                            }
+                        if (i < ncol) {
+                            const J vx = vp[i], vy = vq[i];
+                            vp[i] = cs * vx - sn * vy;
+                            vq[i] = sn * vx + cs * vy;
                         }
-                        if (l16 == 0) {
-                            alpha[p] = a - t * g;
-                            alpha[q] = b + t * g;
-                            *s_flag = 1;
-                        }
+                    }
+                    if (lp == 0) {
+                        alpha[p] = a - t * g;
+                        alpha[q] = b + t * g;
+                        *s_flag = 1;
                     }
                 }
             }
-            __syncthreads();
+          }
+            bar_sync_1(nwork);
         }
         const int rotated = s_flag[0], big = s_flag[1];
-        __syncthreads();
+        bar_sync_1(nwork);
         if (tid == 0) s_flag[1] = 0;
         if (!rotated) break;
         if (!big) {
             ++sweep;
-            for (int c = tid; c < ncol; c += bd) {
+            for (int c = tid; c < ncol; c += nwork) {
                 J s = 0;
                 for (int i = 0; i < nrow; ++i) s = fma(B[(size_t)c * ldb + i], B[(size_t)c * ldb + i], s);
                 alpha[c] = s;
             }
-            __syncthreads();
             break;
         }
     }
     return sweep;
 }
 
+// Half-warp pairs: 4 elements per lane up to 64 columns, 10 above.
 template <typename J>
 __device__ int jacobi_hw(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *alpha, J tol, int max_sweeps,
                          int *s_flag) {
-    if (nrow <= 64 && ncol <= 64) return jacobi_hw_n<J, 4>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
-    return jacobi_hw_n<J, 10>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
+    if (nrow <= 64 && ncol <= 64) return jacobi_lp<J, 16, 4>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
+    return jacobi_lp<J, 16, 10>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
 }
 
 // rank of each of n keys in descending order (ties by index) -> order[rank] = i
@@ -730,10 +740,14 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     }
     __syncthreads();
     const J eps_j = f32 ? (J)1.1920928955078125e-07 : (J)2.220446049250313e-16;
-    const J tol = (J)2 * sqrt((J)nc) * eps_j;
+    // FP64: n eps, above the rounding error of the computed b_p . b_q, so
+    // that the sweeps end; FP32: the double-float finish below carries the
+    // accuracy and a tighter rotation threshold pays off
+    const J tol = f32 ? (J)2 * sqrt((J)nc) * eps_j : (J)nc * eps_j;
     clk[1] = clock64();
     if (tid == 0) s_flag[1] = 0;
     const int nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, f32 ? 20 : 30, s_flag);
+    __syncthreads();
     clk[2] = clock64();
     sort_desc<J>(alpha, nc, order);
     const int rsel = a.r < nc ? a.r : nc;
@@ -804,7 +818,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     clk[3] = clock64();
     // truncation: keep min(r, #sigma > nc u sigma_1)
     if (tid == 0) {
-        const double s0 = XOps<X>::to(sig[0]);
+        const double s0 = rsel > 0 ? XOps<X>::to(sig[0]) : 0.0;
         const double thr = nc * u * s0;
         int keepn = 0;
         for (int s = 0; s < rsel; ++s)
@@ -960,7 +974,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_chol(RefineArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
+__global__ void __launch_bounds__(CORE_THREADS) k_refine_svd(RefineArgs a) {
     const int r = a.r;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Carve cv{smem_raw};
@@ -1001,7 +1015,9 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
         V[q * r + p] = (p == q) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_hw<double>(B, r, r, r, V, r, alpha, 2.0 * sqrt((double)r) * 2.220446049250313e-16, 40, s_flag);
+    // threshold n eps: above the rounding error of the computed dot products
+    jacobi_hw<double>(B, r, r, r, V, r, alpha, (double)r * 2.220446049250313e-16, 40, s_flag);
+    __syncthreads();
     sort_desc<double>(alpha, r, order);
     // sigma_s, V_R[:, s], U_R[:, s] = B[:, order[s]] / sigma_s, K = R^{-1} U_R
     for (int s = tid; s < r; s += bd) a.sigma[s] = sqrt(alpha[order[s]]);
@@ -1021,18 +1037,20 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_refine_svd(RefineArgs a) {
 
 // ---------------------------------------------------------------------------
 // ICRS (Algorithm 1, GET UPDATE with rows): the top right singular vectors
-// V_r of the scaled row block W from its Gram G_W = W^T W (g x g, FP64,
-// ld cmax).  G_W = R^T R (Cholesky with dropped dependent pivots), then
-// one-sided Jacobi on the columns of R: R V = B, so V diagonalises G_W and
-// the column norms of B are the singular values of W.  V_r = the columns of
-// V for the rc = min(r, g) largest, written as the coefficient block of the
-// pass C = D V_r (Ym[j * rmax + s]).  The state of that pass is stc =
-// {r_cur 0, g, r_new rc}; the round's block width becomes rc.
+// V_r of the scaled row block W are the top eigenvectors of G_W = W^T W
+// (g x g, FP64, ld cmax).  A Cholesky factorisation of the index-reversed
+// Gram, J G_W J = R^T R (J the reversal), gives the upper triangular
+// R_hat = J R^T J with G_W = R_hat R_hat^T, so the left singular vectors of
+// R_hat are the wanted eigenvectors: the core SVD kernel (k_core) computes
+// them as the merge of the block R_hat into an empty basis.  Its inputs are
+// set up here: R1p = R_hat, G2 = I (second CholeskyQR factor R2 = I) and
+// M1 = I, so that the core's block-coefficient output Y = R^{-1} U_E is U_E
+// itself, and the state stc = {r_cur 0, g}.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CORE_THREADS) k_rows_small(RowsSmallArgs a) {
+template <typename X>
+__global__ void __launch_bounds__(SMALL_THREADS) k_rows_chol(RowsSmallArgs a) {
     DevState *st = a.st;
     const int g = st->g, done = st->done, t = st->t;
-    const int rc = g < a.r ? g : a.r;
     const int tid = threadIdx.x, bd = blockDim.x;
     if (tid == 0) {
         DevState s{};
@@ -1040,56 +1058,61 @@ __global__ void __launch_bounds__(CORE_THREADS) k_rows_small(RowsSmallArgs a) {
         s.t = t;
         s.r_cur = 0;
         s.g = g;
-        s.r_new = rc;
+        s.remaining = st->remaining;
         *a.stc = s;
     }
     if (done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Carve cv{smem_raw};
-    double *W = cv.take<double>((size_t)g * g);
-    double *R = cv.take<double>((size_t)g * g);
-    double *V = cv.take<double>((size_t)g * g);
-    double *alpha = cv.take<double>(g);
-    int *order = cv.take<int>(g);
-    __shared__ int s_flag[2];
+    X *W = cv.take<X>((size_t)g * g);
+    X *R = cv.take<X>((size_t)g * g);
     __shared__ double red[32];
-    __shared__ double piv3[3];
-    if (tid == 0) s_flag[1] = 0;
+    __shared__ X piv3[3];
+    const int cm = a.cmax;
     double dmax = 0.0;
-    for (int j = tid; j < g; j += bd) dmax = a.GW[j * a.cmax + j] > dmax ? a.GW[j * a.cmax + j] : dmax;
+    for (int j = tid; j < g; j += bd) dmax = a.GW[j * cm + j] > dmax ? a.GW[j * cm + j] : dmax;
     dmax = block_max<double>(dmax, red);
     for (int e = tid; e < g * g; e += bd) {
-        const int i = e / g, j = e % g;
-        W[e] = i <= j ? a.GW[i * a.cmax + j] : 0.0;
+        const int i = e / g, j = e % g;   // reversed indices: (i, j) <- (g-1-j, g-1-i), upper part
+        W[e] = XOps<X>::from(i <= j ? a.GW[(g - 1 - j) * cm + (g - 1 - i)] : 0.0);
     }
     __syncthreads();
-    const double eps = g * 1.1102230246251565e-16;
-    chol_drop<double>(W, g, g, eps * eps * dmax, R, g, piv3);
+    const double eps = g * unit_roundoff(a.dtype);
+    chol_drop<X>(W, g, g, XOps<X>::from(eps * eps * dmax), R, g, piv3);
     for (int e = tid; e < g * g; e += bd) {
-        const int q = e / g, p = e % g;   // W <- B, column-major: column q of R
-        W[q * g + p] = R[p * g + q];
-        V[q * g + p] = (p == q) ? 1.0 : 0.0;
+        const int i = e / g, j = e % g;
+        a.R1p[i * cm + j] = i <= j ? XOps<X>::to(R[(g - 1 - j) * g + (g - 1 - i)]) : 0.0;
+        a.G2[i * cm + j] = i == j ? 1.0 : 0.0;
+        a.M1[i * cm + j] = i == j ? 1.0 : 0.0;
     }
-    __syncthreads();
-    jacobi_hw<double>(W, g, g, g, V, g, alpha, 2.0 * sqrt((double)g) * 2.220446049250313e-16, 40, s_flag);
-    sort_desc<double>(alpha, g, order);
-    for (int e = tid; e < g * rc; e += bd) {
-        const int j = e / rc, s = e % rc;
-        a.Ym[j * a.rmax + s] = V[order[s] * g + j];
-    }
-    __syncthreads();
-    if (tid == 0) st->g = rc;
 }
 
-size_t rows_small_smem(int cmax) {
-    return 3 * al16x((size_t)cmax * cmax * 8) + al16x((size_t)cmax * 8) + al16x((size_t)cmax * 4) + 64;
+// End of the ICRS block step: the round's block width becomes the number of
+// kept right vectors; a non-finite value seen by the core is reported.
+__global__ void k_rows_setg(DevState *st, const DevState *stc) {
+    if (threadIdx.x != 0 || st->done) return;
+    st->g = stc->r_new;
+    if (stc->status != 0) st->status = stc->status;
 }
 
-pod_status launch_rows_small(const RowsSmallArgs &a, cudaStream_t s) {
+size_t rows_small_smem(int cmax) { return 2 * al16x((size_t)cmax * cmax * 8) + 64; }
+
+pod_status launch_rows_chol(const RowsSmallArgs &a, cudaStream_t s) {
     const size_t smem = rows_small_smem(a.cmax);
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
-    POD_CUDA_TRY(cudaFuncSetAttribute(k_rows_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_rows_small<<<1, CORE_THREADS, smem, s>>>(a);
+    if (a.dtype == POD_F32 && !a.core_f64) {
+        POD_CUDA_TRY(cudaFuncSetAttribute(k_rows_chol<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_rows_chol<dfloat><<<1, SMALL_THREADS, smem, s>>>(a);
+    } else {
+        POD_CUDA_TRY(cudaFuncSetAttribute(k_rows_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_rows_chol<double><<<1, SMALL_THREADS, smem, s>>>(a);
+    }
+    POD_CUDA_TRY(cudaGetLastError());
+    return POD_OK;
+}
+
+pod_status launch_rows_setg(DevState *st, const DevState *stc, cudaStream_t s) {
+    k_rows_setg<<<1, 32, 0, s>>>(st, stc);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }
@@ -1107,7 +1130,7 @@ pod_status launch_refine_svd(const RefineArgs &a, cudaStream_t s) {
     const size_t smem = 8 * al16x((size_t)a.r * a.r * 8) + al16x((size_t)a.r * 8) + al16x((size_t)a.r * 4) + 64;
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     POD_CUDA_TRY(cudaFuncSetAttribute(k_refine_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_refine_svd<<<1, SMALL_THREADS, smem, s>>>(a);
+    k_refine_svd<<<1, CORE_THREADS, smem, s>>>(a);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }

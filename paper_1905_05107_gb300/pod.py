@@ -33,7 +33,7 @@ EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay
 
 ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "core_svd", "update", "finish"]
 ORT_KERNELS = ["ort_atu", "ort_values"]
-ROW_KERNELS = ["rows_sample", "rows_gram", "rows_svd", "rows_block"]
+ROW_KERNELS = ["rows_sample", "rows_gram", "rows_chol", "rows_core", "rows_block", "rows_setg"]
 
 
 class PodParams(ctypes.Structure):
