@@ -43,6 +43,23 @@ K_MODES, C_DRAWS, TOL = 20, 40, 1e-8
 METRIC = "time-to-k-POD-modes (s)"
 WORKLOAD = "flow-316x316x2000-f32"
 
+# FP32 SIMT peak of a GB300 from its unit counts and clock: 152 SMs x 128
+# FP32 lanes x 2 flop (FMA) x 2.07 GHz; and the same for one SM.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_SM_PEAK_GFLOPS = 128 * 2 * 2.07e9 / 1e9
+
+# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the kernel as it was when captured; the hash of
+# its sources at that time guards against reporting stale counters.
+NCU_TRAFFIC = {
+    # profiles/k_core_flow316x316x2000_f32.md: 221.7 KB read, 0 written
+    "core_svd": {"bytes": 221696, "src_sha": "7be72e2469ee98c5"},
+}
+KERNEL_SOURCES = {
+    "core_svd": ["paper_1905_05107_gb300/csrc/small.cu", "paper_1905_05107_gb300/csrc/common.cuh",
+                 "paper_1905_05107_gb300/csrc/pod_internal.h"],
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -57,6 +74,22 @@ def parse():
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def sources_sha(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec or rec["src_sha"] != sources_sha(kernel):
+        return None
+    return rec["bytes"]
 
 
 def load_peaks():
@@ -311,7 +344,7 @@ def run_ours(args):
     totals = {kname: float(np.sum(v)) for kname, v in per.items()}
     dominant = max(totals, key=totals.get)
     hbm, bf16, peak_kind = load_peaks()
-    # algorithmic bytes of every launch of each modelled kernel (round t has
+    # algorithmic bytes of every launch of each streaming kernel (round t has
     # r_t = 0 modes in round 0 and K_MODES after, g_t distinct columns)
     moved = {}
     for t, g in enumerate(rg):
@@ -319,17 +352,39 @@ def run_ours(args):
         for kname in ("proj", "cgs_gram", "qr2_gram", "update"):
             moved[kname] = moved.get(kname, 0.0) + mdl[kname][0]
     moved["colnorms"] = kernel_model(m, n, es, K_MODES, C_DRAWS)["colnorms"][0] * len(per["colnorms"])
-    roof_kernel = dominant if dominant in moved else max((k for k in totals if k in moved), key=totals.get)
-    launches_k = len(per[roof_kernel])
-    avg_ms = totals[roof_kernel] / launches_k
-    bytes_ = moved[roof_kernel] / launches_k
-    achieved = bytes_ / (avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": roof_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
-                "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs" % peak_kind,
-                "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms,
-                "time_share": {k: round(totals[k] / sum(totals.values()), 4) for k in totals},
-                "dominant_kernel": dominant}
+    hbm_kernels = {}
+    for kname, b in moved.items():
+        gbs = b / (totals[kname] * 1e-3) / 1e9
+        hbm_kernels[kname] = {"GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4)}
+    # the core SVD: one CTA, one-sided Jacobi on the (r + g)-wide core;
+    # algorithmic flops 6 n_c^3 per sweep (n_c = r_t + g_t)
+    core_flops = 0.0
+    for t, g in enumerate(rg):
+        nc = (0 if t == 0 else K_MODES) + g
+        core_flops += 6.0 * nc ** 3 * (sweeps[t] if t < len(sweeps) else 0)
+    if dominant == "core_svd":
+        launches_k = len(per["core_svd"])
+        avg_ms = totals["core_svd"] / launches_k
+        achieved = core_flops / launches_k / (avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "core_svd", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ncu_traffic("core_svd"),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (FP32 FMA)",
+                    "algorithmic_flops_per_launch": core_flops / launches_k, "avg_launch_ms": avg_ms,
+                    "note": "one CTA on one of 152 SMs, latency-bound Jacobi rounds; frac of that SM's "
+                            "FP32 peak: %.4f" % (achieved * 1e3 / FP32_SM_PEAK_GFLOPS)}
+    else:
+        roof_kernel = dominant if dominant in moved else max((k for k in totals if k in moved), key=totals.get)
+        launches_k = len(per[roof_kernel])
+        avg_ms = totals[roof_kernel] / launches_k
+        bytes_ = moved[roof_kernel] / launches_k
+        achieved = bytes_ / (avg_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": roof_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": ncu_traffic(roof_kernel),
+                    "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs" % peak_kind,
+                    "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms}
+    roofline["time_share"] = {k: round(totals[k] / sum(totals.values()), 4) for k in totals}
+    roofline["dominant_kernel"] = dominant
+    roofline["hbm_kernels"] = hbm_kernels
     core_phase = np.mean(np.array(core_cyc, dtype=np.float64), axis=0).tolist() if core_cyc else []
 
     cpu = None
