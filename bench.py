@@ -76,6 +76,25 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value (the slowest replica sets the time);
+    `device` is where the collective's buffer lives (cuda for NCCL, cpu for
+    gloo)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def sources_sha(kernel):
     import hashlib
     h = hashlib.sha256()
@@ -259,8 +278,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         rounds = ctx.counters()[1]
         # ------------------------------------------------ device-timed steps
-        if world > 1:
-            torch.distributed.barrier()
+        barrier(world)
         torch.cuda.synchronize()
         clocks = ClockSampler(dev.index)
         clocks.start()
@@ -275,11 +293,8 @@ def run_ours(args):
         l1, _ = ctx.counters()
         clk = clocks.stop()
         ms = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-            torch.distributed.barrier()
+        ms = max_over_ranks(ms, world, dev)
+        barrier(world)
         launches = (l1 - l0) // args.steps
         # ------------------------------------------------ end-to-end steps
         U_host = torch.empty((K_MODES, m), dtype=torch.float32).pin_memory()
@@ -293,8 +308,7 @@ def run_ours(args):
 
         step_e2e()
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        barrier(world)
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -303,10 +317,7 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = f0.elapsed_time(f1) / args.steps
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks(ms_e2e, world, dev)
         # ------------------------------------------------ per-kernel timings
         # one more run, round by round, with CUDA events between kernels
         ctx.reset()

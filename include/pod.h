@@ -60,6 +60,8 @@ enum { POD_SUBSPACE = 0, POD_MODES = 1 };
 /* arithmetic of the core SVD of E (Algorithm 2):
  * POD_CORE_AUTO = FP64 for POD_F64 data, FP32 for POD_F32 data */
 enum { POD_CORE_AUTO = 0, POD_CORE_F32 = 1, POD_CORE_F64 = 2 };
+/* arithmetic of the tall projections (P = U^T C, Grams, updates) */
+enum { POD_PREC_F32 = 0, POD_PREC_BF16 = 1, POD_PREC_BF16X3 = 2, POD_PREC_TF32X3 = 3 };
 
 /*
  * Parameters of one POD problem; mirrors ISMA's inputs (A, p, k, c, w, r,
@@ -87,6 +89,14 @@ typedef struct pod_params {
     int32_t dtype;         /* POD_F32 | POD_F64                              */
     int32_t core;          /* POD_CORE_AUTO | POD_CORE_F32 | POD_CORE_F64    */
     uint64_t seed;         /* Philox4x32-10 key                              */
+    int32_t block_trunc;   /* 1: GET UPDATE truncates the new block to rank r
+                              through SVD(D^T D) before the merge (the paper's
+                              literal Algorithm 1); 0: D merges directly     */
+    int32_t precision;     /* POD_PREC_F32 (the only arithmetic of the
+                              projections in this build; others are
+                              POD_EUNSUPPORTED)                              */
+    int32_t keep_tape;     /* reserved for pod_backward; must be 0           */
+    int32_t reserved;      /* must be 0                                      */
 } pod_params;
 
 typedef struct pod_ctx pod_ctx;
@@ -148,6 +158,21 @@ POD_API pod_status pod_modes(pod_ctx *ctx, void *U_dev, double *sigma_dev, void 
  */
 POD_API pod_status pod_get_trace(pod_ctx *ctx, int32_t t, int32_t *idx_host,
                          int32_t *g_host, double *measure_host);
+
+/*
+ * pod_wedin -- the quality measure of the converged solution (Sec. 3.3,
+ * Eq. 7): with the refined top-k triplets (U~_k, sigma~_k, V~_k),
+ * R = A V~_k - U~_k Sigma~_k and S = A^T U~_k - V~_k Sigma~_k, and
+ * omega = min(|sigma~_k - sigma~_{k+1}|, sigma~_k) estimated from the carried
+ * singular values, out4 (host, 4 doubles) receives
+ *   { sqrt(|R|_F^2 + |S|_F^2) / omega, |R|_F, |S|_F, omega }.
+ * One extra pass over A (R); S comes from the refinement's A^T U.
+ * Needs pod_modes to have run with refine = 1 (else POD_ESTATE) and r >= k + 1
+ * carried modes (else POD_EUNSUPPORTED: sigma~_{k+1} does not exist).
+ * Allocates its O(n k) workspace for the call; synchronises the stream.
+ * Errors: POD_EINVAL, POD_ESTATE, POD_EUNSUPPORTED, POD_ENOMEM, POD_ECUDA.
+ */
+POD_API pod_status pod_wedin(pod_ctx *ctx, double *out4);
 
 /*
  * pod_last_rows -- the row sample of the most recent ICRS iteration (SAMPLE

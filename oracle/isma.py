@@ -15,6 +15,7 @@ What it follows (arXiv 1905.05107, Charumathi, Ramakrishna, Vasudevan):
   of the subspaces) and the closing refinement QR(A^T U), SVD(R).
 * Algorithm 3 (incremental POD over column blocks), Sec. 4.2.
 * Eq. 3 and Eq. 5 for default sample counts.
+* The quality measure of Sec. 3.3 (Wedin's bound, Eq. 7).
 
 Everything is NumPy FP64; LAPACK (``numpy.linalg.qr`` / ``svd``) serves as the
 QR and SVD steps, exactly as the paper's SciPy/LAPACK runs did (Sec. 4).  The
@@ -315,6 +316,7 @@ class Result:
     V: Optional[np.ndarray]
     trace: List[IterRecord] = field(default_factory=list)
     converged: bool = False
+    sigma_all: Optional[np.ndarray] = None   # all r carried singular values
 
     @property
     def iterations(self) -> int:
@@ -408,9 +410,36 @@ def isma(A: np.ndarray, p: Params) -> Result:
     if p.refine and U.shape[1] > 0:
         U, sig, V = refine(A, U)
     kk = min(p.k, U.shape[1])
+    sig_all = sig.copy()
     U, V = U[:, :kk], (V[:, :kk] if V is not None else None)
     U, V = fix_signs(U, V, p.seed)
-    return Result(U=U, sigma=sig[:kk], V=V, trace=trace, converged=converged)
+    return Result(U=U, sigma=sig[:kk], V=V, trace=trace, converged=converged, sigma_all=sig_all)
+
+
+# ----------------------------------------------------------------------------
+# Quality of the converged solution (Sec. 3.3, Eq. 7)
+# ----------------------------------------------------------------------------
+@dataclass
+class Wedin:
+    bound: float
+    norm_R: float
+    norm_S: float
+    omega: float
+
+
+def wedin_measure(A: np.ndarray, U: np.ndarray, sigma: np.ndarray, V: np.ndarray,
+                  sigma_next: float) -> Wedin:
+    """Right-hand side of Eq. 7 for the approximate top-k triplets
+    (U, sigma, V): R = A V - U diag(sigma), S = A^T U - V diag(sigma), and
+    omega estimated from the approximate singular values as
+    min(|sigma_k - sigma_{k+1}|, sigma_k)."""
+    A = np.asarray(A, dtype=np.float64)
+    R = A @ V - U * sigma[None, :]
+    S = A.T @ U - V * sigma[None, :]
+    nR, nS = float(np.linalg.norm(R)), float(np.linalg.norm(S))
+    sk = float(sigma[-1])
+    omega = min(abs(sk - float(sigma_next)), sk)
+    return Wedin(bound=math.sqrt(nR * nR + nS * nS) / omega, norm_R=nR, norm_S=nS, omega=omega)
 
 
 # ----------------------------------------------------------------------------

@@ -172,6 +172,10 @@ static pod_status check_params(const pod_params *p) {
     if (p->rows != 0 && p->rows != 1) return POD_EINVAL;
     if (p->row_strategy != POD_ROW_L2N && p->row_strategy != POD_ROW_LS) return POD_EINVAL;
     if (p->w < 0) return POD_EINVAL;
+    if (p->block_trunc != 0 && p->block_trunc != 1) return POD_EINVAL;
+    if (p->precision < POD_PREC_F32 || p->precision > POD_PREC_TF32X3) return POD_EINVAL;
+    if (p->precision != POD_PREC_F32 || p->keep_tape != 0) return POD_EUNSUPPORTED;
+    if (p->reserved != 0) return POD_EINVAL;
     if (p->c > 256 || (p->r > 0 ? p->r : p->k) > 256) return POD_EUNSUPPORTED;
     if (!(p->tol == p->tol)) return POD_EINVAL;
     return POD_OK;
@@ -293,9 +297,10 @@ static pod_status enqueue_round(pod_ctx *c) {
     mark(c);
 
     TallArgs<T> ta = tall_args<T>(c, c->part, (int64_t)c->rmax * c->cmax);
-    if (c->p.rows) {
-        // GET UPDATE with rows: W from sampled rows of D, V_r from W^T W,
-        // then the merge takes the materialised block C = D V_r
+    if (c->p.rows || c->p.block_trunc) {
+        // GET UPDATE with rows (ICRS): W from sampled rows of D, V_r from
+        // W^T W; or the literal truncation of the new block (W = D, all rows,
+        // unit scale); the merge then takes the materialised block C = D V_r
         RowArgs<T> ra{};
         ra.m = c->p.m;
         ra.A = (const T *)c->A;
@@ -330,9 +335,12 @@ static pod_status enqueue_round(pod_ctx *c) {
         ra.gsum = c->gsum_w;
         ra.gcounters = c->counters_w;
         ra.GW = c->GW;
-        POD_TRY(launch_rows<T>(ra, s, c->sms));
-        c->launches += ROW_KERNELS - 1;
-        mark(c);
+        ra.all_rows = c->p.rows ? 0 : 1;
+        if (c->p.rows) {
+            POD_TRY(launch_rows<T>(ra, s, c->sms));
+            c->launches += ROW_KERNELS - 1;
+            mark(c);
+        }
         POD_TRY(launch_row_gram<T>(ra, s));
         mark(c);
         RowsSmallArgs rs{};
@@ -599,10 +607,12 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         c->wdraws = (int)(p->w > 0 ? p->w : default_row_draws(p->k, p->m));   // draws with replacement: w may exceed m
         c->rnb = row_blocks(p->m);
         c->gplan = row_gram_plan(p->dtype, c->wdraws, c->cmax, c->sms);
-        if (rows_small_smem(c->cmax) > 220 * 1024) {
-            free(c);
-            return POD_EUNSUPPORTED;
-        }
+    } else if (p->block_trunc) {
+        c->gplan = row_gram_plan(p->dtype, p->m, c->cmax, c->sms);
+    }
+    if ((p->rows || p->block_trunc) && rows_small_smem(c->cmax) > 220 * 1024) {
+        free(c);
+        return POD_EUNSUPPORTED;
     }
     if (core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) > 220 * 1024 ||
         small_chol_smem(c->cmax) > 220 * 1024 || c->plan.smem > 227 * 1024) {
@@ -670,6 +680,8 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         ALLOC(c->r_rcnt, c->wdraws);
         ALLOC(c->r_rscale, c->wdraws);
         ALLOC(c->r_h, 1);
+    }
+    if (p->rows || p->block_trunc) {
         unsigned char *Cb = nullptr;
         ALLOC(Cb, (size_t)m * rm * es);
         c->Cbuf = Cb;
@@ -709,8 +721,9 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (p->rows) {
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_cnt, 0, (size_t)m * sizeof(unsigned), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_h, 0, sizeof(int32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->counters_w, 0, (c->gplan.groups + 1) * sizeof(unsigned), s);
     }
+    if (p->rows || p->block_trunc)
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->counters_w, 0, (c->gplan.groups + 1) * sizeof(unsigned), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ctx_free(c);
@@ -863,6 +876,88 @@ pod_status pod_last_rows(pod_ctx *c, int32_t *rows_host, int32_t *counts_host, i
     if (hh > 0 && counts_host)
         POD_CUDA_TRY(cudaMemcpyAsync(counts_host, c->r_rcnt, (size_t)hh * 4, cudaMemcpyDeviceToHost, c->stream));
     POD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return POD_OK;
+}
+
+pod_status pod_wedin(pod_ctx *c, double *out4) {
+    if (!c || !out4) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (!c->refined) return POD_ESTATE;
+    const int k = c->p.k, r = c->refined_r;
+    if (r < k + 1) return POD_EUNSUPPORTED;
+    cudaStream_t s = c->stream;
+    const int64_t m = c->p.m, n = c->p.n;
+    const int gn = wedin_grid_n(n), gm = wedin_grid_m(m), passes = wedin_passes(k);
+    const int grn = (gn + RED_GROUP - 1) / RED_GROUP, grm = (gm + RED_GROUP - 1) / RED_GROUP;
+    // workspace for this call (released before returning)
+    double *Vk = nullptr, *part = nullptr, *out = nullptr;
+    float2 *Vkf = nullptr;
+    unsigned *cnt = nullptr;
+    pod_status st = dalloc(&Vk, (size_t)n * k);
+    if (st == POD_OK) st = dalloc(&Vkf, (size_t)n * k);
+    const size_t np = (size_t)gn + grn + 1 + gm + grm + 1;
+    if (st == POD_OK) st = dalloc(&part, np);
+    if (st == POD_OK) st = dalloc(&out, 1 + passes);
+    if (st == POD_OK) st = dalloc(&cnt, (size_t)grn + 1 + grm + 1);
+    double host[2 + 64] = {0};
+    double sig2[2] = {0, 0};
+    if (st == POD_OK) {
+        WedinArgs a{};
+        a.m = m;
+        a.n = n;
+        a.lda = c->p.lda;
+        a.k = k;
+        a.r = r;
+        a.Y = c->Y;
+        a.K = c->rK;
+        a.VR = c->rVR;
+        a.sigma = c->sigma;
+        a.Vk = Vk;
+        a.Vkf = Vkf;
+        a.part_s = part;
+        a.gsum_s = part + gn;
+        a.part_r = part + gn + grn + 1;
+        a.gsum_r = a.part_r + gm;
+        a.out = out;
+        a.counters_v = cnt;
+        a.counters_r = cnt + grn + 1;
+        cudaError_t e = cudaMemsetAsync(cnt, 0, ((size_t)grn + 1 + grm + 1) * sizeof(unsigned), s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = POD_ECUDA;
+        }
+        if (st == POD_OK)
+            st = c->p.dtype == POD_F32 ? launch_wedin<float>(a, (const float *)c->A, (const float *)c->U, s)
+                                       : launch_wedin<double>(a, (const double *)c->A, (const double *)c->U, s);
+        c->launches += 1 + passes;
+        if (st == POD_OK && passes + 1 <= 64) {
+            if (cudaMemcpyAsync(host, out, (1 + passes) * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(sig2, c->sigma + (k - 1), 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                cudaGetLastError();
+                st = POD_ECUDA;
+            }
+        } else if (st == POD_OK) {
+            st = POD_EUNSUPPORTED;
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(Vk);
+    cudaFree(Vkf);
+    cudaFree(part);
+    cudaFree(out);
+    cudaFree(cnt);
+    if (st != POD_OK) return st;
+    double r2 = 0.0;
+    for (int p = 0; p < passes; ++p) r2 += host[1 + p];
+    const double s2 = host[0];
+    const double sk = sig2[0], sk1 = sig2[1];
+    const double gap = fabs(sk - sk1);
+    const double omega = gap < sk ? gap : sk;
+    out4[0] = sqrt(r2 + s2) / omega;
+    out4[1] = sqrt(r2);
+    out4[2] = sqrt(s2);
+    out4[3] = omega;
     return POD_OK;
 }
 

@@ -143,6 +143,7 @@ struct RowArgs {
     int32_t *h;             // distinct rows
     // Gram pass: ggrid CTAs of rows_per rows (shared column stride lds)
     int ggrid, rows_per, lds;
+    int all_rows;           // 1: W = D (all m rows, unit scale)
     double *part;           // ggrid x cmax^2
     double *gsum;           // (groups + 1) x cmax^2
     unsigned *gcounters;    // groups + 1, zero between launches
@@ -151,12 +152,30 @@ struct RowArgs {
 struct RowGramPlan {
     int grid, rows_per, lds, groups;
 };
-RowGramPlan row_gram_plan(int dtype, int wdraws, int cmax, int sms);
+RowGramPlan row_gram_plan(int dtype, int64_t wdraws, int cmax, int sms);
 template <typename T>
 pod_status launch_rows(const RowArgs<T> &a, cudaStream_t s, int sms);
 template <typename T>
 pod_status launch_row_gram(const RowArgs<T> &a, cudaStream_t s);
 int row_blocks(int64_t m);
+
+// ------------------------------------------------------------------ wedin.cu
+// Eq. 7 residual norms after the refinement (see wedin.cu).
+struct WedinArgs {
+    int64_t m, n, lda;
+    int k, r;
+    const double *Y, *K, *VR, *sigma;   // Y = A^T U (n x r), refinement K and V_R (r x r)
+    double *Vk;                         // n x k
+    float2 *Vkf;                        // n x k, double-float copy
+    double *part_s, *gsum_s, *part_r, *gsum_r;
+    double *out;                        // [0] = |S|^2, [1 + p] = |R|^2 of pass p
+    unsigned *counters_v, *counters_r;  // zero between launches
+};
+int wedin_grid_n(int64_t n);
+int wedin_grid_m(int64_t m);
+int wedin_passes(int k);
+template <typename T>
+pod_status launch_wedin(const WedinArgs &a, const T *A, const T *U, cudaStream_t s);
 
 // ------------------------------------------------------------------ small.cu
 pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t count,

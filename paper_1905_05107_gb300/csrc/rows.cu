@@ -211,7 +211,9 @@ __global__ void __launch_bounds__(RB) k_row_compact(RowArgs<T> a) {
 }
 
 // G_W = W^T W without materialising W: each CTA gathers its share of the h
-// scaled rows (row l of W = d^{I_r[l]} * scale_l) into shared memory and
+// scaled rows (row l of W = d^{I_r[l]} * scale_l; with all_rows, W = D: all
+// m rows, unit scale, for the literal truncation of the new block) into
+// shared memory and
 // forms its partial Gram; the partials are summed in a fixed order in FP64.
 // FP32 data: the eigenvectors of a Gram formed in FP32 lose accuracy as
 // sigma_1^2 / (sigma_r^2 - sigma_{r+1}^2), so every product is split exactly
@@ -224,13 +226,21 @@ __global__ void __launch_bounds__(256) k_row_gram(RowArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Ws = reinterpret_cast<T *>(smem_raw);   // column j at j * lds
     __shared__ int s_flag;
-    const int g = st->g, h = a.h[0];
+    const int g = st->g;
+    const int64_t h = a.all_rows ? a.m : (int64_t)a.h[0];
     const int rp = a.rows_per, lds = a.lds;
-    const int r0 = blockIdx.x * rp;
-    const int nr = max(0, min(rp, h - r0));
-    for (int e = threadIdx.x; e < nr * g; e += blockDim.x) {
-        const int j = e / nr, l = e - j * nr;
-        Ws[j * lds + l] = (T)((double)a.A[(int64_t)a.idx[j] * a.lda + a.rows[r0 + l]] * a.rscale[r0 + l]);
+    const int64_t r0 = (int64_t)blockIdx.x * rp;
+    const int nr = (int)max((int64_t)0, min((int64_t)rp, h - r0));
+    if (a.all_rows) {
+        for (int e = threadIdx.x; e < nr * g; e += blockDim.x) {
+            const int j = e / nr, l = e - j * nr;
+            Ws[j * lds + l] = a.A[(int64_t)a.idx[j] * a.lda + r0 + l];
+        }
+    } else {
+        for (int e = threadIdx.x; e < nr * g; e += blockDim.x) {
+            const int j = e / nr, l = e - j * nr;
+            Ws[j * lds + l] = (T)((double)a.A[(int64_t)a.idx[j] * a.lda + a.rows[r0 + l]] * a.rscale[r0 + l]);
+        }
     }
     __syncthreads();
     const int cm = a.cmax;
@@ -292,16 +302,16 @@ pod_status launch_row_gram(const RowArgs<T> &a, cudaStream_t s) {
 
 int row_blocks(int64_t m) { return (int)((m + RB - 1) / RB); }
 
-RowGramPlan row_gram_plan(int dtype, int wdraws, int cmax, int sms) {
+RowGramPlan row_gram_plan(int dtype, int64_t wdraws, int cmax, int sms) {
     RowGramPlan p{};
     const size_t es = dtype == POD_F32 ? 4 : 8;
     const int max_rows = (int)((96 * 1024) / ((size_t)cmax * es)) - 1;   // shared-memory cap per CTA
-    int grid = 2 * sms;
+    int64_t grid = 2 * sms;
     if ((wdraws + grid - 1) / grid > max_rows) grid = (wdraws + max_rows - 1) / max_rows;
     if (grid > (wdraws + 15) / 16) grid = (wdraws + 15) / 16;
     if (grid < 1) grid = 1;
-    p.grid = grid;
-    p.rows_per = (wdraws + grid - 1) / grid;
+    p.grid = (int)grid;
+    p.rows_per = (int)((wdraws + grid - 1) / grid);
     p.lds = p.rows_per | 1;   // odd column stride: conflict-free shared loads across columns
     p.groups = (grid + RED_GROUP - 1) / RED_GROUP;
     return p;

@@ -16,6 +16,9 @@
 namespace {
 
 constexpr int SMALL_THREADS = 1024;
+// The one-CTA Cholesky kernels take a barrier per elimination step; with
+// O(n^2 / 4) work per step, 8 warps finish a step sooner than 32.
+constexpr int CHOL_THREADS = 256;
 constexpr int CORE_THREADS = 512;
 
 __device__ __forceinline__ double unit_roundoff(int dtype) {
@@ -390,7 +393,7 @@ pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t
 // R1p = M1^{-1} (the exact inverse of what was applied, used in E).
 // ---------------------------------------------------------------------------
 template <typename X>
-__global__ void __launch_bounds__(SMALL_THREADS) k_small_chol(SmallArgs a) {
+__global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     DevState *st = a.st;
     if (st->done) return;
     const int r = st->r_cur, g = st->g, nc = r + g;
@@ -453,10 +456,10 @@ pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s) {
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     if (a.dtype == POD_F32) {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_small_chol<dfloat><<<1, SMALL_THREADS, smem, s>>>(a);
+        k_small_chol<dfloat><<<1, CHOL_THREADS, smem, s>>>(a);
     } else {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_small_chol<double><<<1, SMALL_THREADS, smem, s>>>(a);
+        k_small_chol<double><<<1, CHOL_THREADS, smem, s>>>(a);
     }
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
@@ -945,7 +948,7 @@ pod_status launch_finish(DevState *st, cudaStream_t s) {
 // FP64 on the columns of R with accumulated V_R; outputs sigma = S_R,
 // VR (U <- U V_R) and K = R^{-1} U_R (V <- Y K = Q U_R).  One CTA.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SMALL_THREADS) k_refine_chol(RefineArgs a) {
+__global__ void __launch_bounds__(CHOL_THREADS) k_refine_chol(RefineArgs a) {
     const int r = a.r;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Carve cv{smem_raw};
@@ -1048,7 +1051,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_refine_svd(RefineArgs a) {
 // itself, and the state stc = {r_cur 0, g}.
 // ---------------------------------------------------------------------------
 template <typename X>
-__global__ void __launch_bounds__(SMALL_THREADS) k_rows_chol(RowsSmallArgs a) {
+__global__ void __launch_bounds__(CHOL_THREADS) k_rows_chol(RowsSmallArgs a) {
     DevState *st = a.st;
     const int g = st->g, done = st->done, t = st->t;
     const int tid = threadIdx.x, bd = blockDim.x;
@@ -1102,10 +1105,10 @@ pod_status launch_rows_chol(const RowsSmallArgs &a, cudaStream_t s) {
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     if (a.dtype == POD_F32 && !a.core_f64) {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_rows_chol<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_rows_chol<dfloat><<<1, SMALL_THREADS, smem, s>>>(a);
+        k_rows_chol<dfloat><<<1, CHOL_THREADS, smem, s>>>(a);
     } else {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_rows_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_rows_chol<double><<<1, SMALL_THREADS, smem, s>>>(a);
+        k_rows_chol<double><<<1, CHOL_THREADS, smem, s>>>(a);
     }
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
@@ -1121,7 +1124,7 @@ pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s) {
     const size_t smem = 4 * al16x((size_t)a.r * a.r * 8) + 64;
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     POD_CUDA_TRY(cudaFuncSetAttribute(k_refine_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_refine_chol<<<1, SMALL_THREADS, smem, s>>>(a);
+    k_refine_chol<<<1, CHOL_THREADS, smem, s>>>(a);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }

@@ -25,11 +25,12 @@ POD_L2N, POD_UNF, POD_ORT = 0, 1, 2
 POD_ROW_L2N, POD_ROW_LS = 0, 1
 POD_SUBSPACE, POD_MODES = 0, 1
 POD_CORE_AUTO, POD_CORE_F32, POD_CORE_F64 = 0, 1, 2
+POD_PREC_F32, POD_PREC_BF16, POD_PREC_BF16X3, POD_PREC_TF32X3 = 0, 1, 2, 3
 
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
             "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
-            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws"]
+            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin"]
 
 ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "core_svd", "update", "finish"]
 ORT_KERNELS = ["ort_atu", "ort_values"]
@@ -43,7 +44,8 @@ class PodParams(ctypes.Structure):
         ("rows", ctypes.c_int32), ("col_strategy", ctypes.c_int32), ("row_strategy", ctypes.c_int32),
         ("criterion", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
         ("refine", ctypes.c_int32), ("dtype", ctypes.c_int32), ("core", ctypes.c_int32),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("block_trunc", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("keep_tape", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -149,7 +151,7 @@ class Context:
     def __init__(self, A, k: int, c: int, r: int = 0, col_strategy: str = "unf",
                  criterion: str = "subspace", tol: float = 1e-8, max_iter: int = 0,
                  refine: bool = True, seed: int = 0x5107, core: str = "auto", rows: bool = False,
-                 row_strategy: str = "l2n", w: int = 0, stream=None):
+                 row_strategy: str = "l2n", w: int = 0, block_trunc: bool = False, stream=None):
         import torch
         _check_colmajor(A)
         self.A = A                    # keeps the borrowed buffer alive
@@ -172,6 +174,7 @@ class Context:
         p.dtype = _dtype_code(A)
         p.core = _CORE[core]
         p.seed = int(seed) & ((1 << 64) - 1)
+        p.block_trunc = 1 if block_trunc else 0
         self.params = p
         self._h = ctypes.c_void_p()
         with torch.cuda.device(A.device):
@@ -227,7 +230,8 @@ class Context:
         cnt = ctypes.c_int32(0)
         _check(lib().pod_round_timings(self._h, buf, 32, ctypes.byref(cnt)), "pod_round_timings")
         names = (ORT_KERNELS if self.params.col_strategy == POD_ORT else []) + ROUND_KERNELS[:1] + \
-            (ROW_KERNELS if self.params.rows else []) + ROUND_KERNELS[1:]
+            (ROW_KERNELS if self.params.rows else (ROW_KERNELS[1:] if self.params.block_trunc else [])) + \
+            ROUND_KERNELS[1:]
         return dict(zip(names, [float(x) for x in buf[: cnt.value]]))
 
     def counters(self):
@@ -249,6 +253,13 @@ class Context:
         meas = ctypes.c_double(0.0)
         _check(lib().pod_get_trace(self._h, int(t), idx, ctypes.byref(g), ctypes.byref(meas)), "pod_get_trace")
         return np.array(idx[: g.value], dtype=np.int64), float(meas.value)
+
+    def wedin(self):
+        """Eq. 7 measure after pod_modes with refinement: dict with the bound,
+        |R|_F, |S|_F and the estimated omega."""
+        out = (ctypes.c_double * 4)()
+        _check(lib().pod_wedin(self._h, out), "pod_wedin")
+        return {"bound": out[0], "norm_R": out[1], "norm_S": out[2], "omega": out[3]}
 
     def row_draws(self) -> int:
         """w, the row draws per ICRS iteration (0 without rows)."""

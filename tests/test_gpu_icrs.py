@@ -158,3 +158,60 @@ def test_icrs_flow_f32_full_size():
     check_trace(g, ref)
     np.testing.assert_allclose(g["sigma"], ref.sigma, rtol=1e-5)
     assert O.sin_principal_max(ref.U, g["U"]) <= 1e-5
+
+
+# ------------------------------------------------ literal GET UPDATE truncation
+def run_literal(A, k, c, **kw):
+    ctx = pod.Context(to_dev(A), k, c, block_trunc=True, **kw)
+    done, meas, steps = ctx.iterate()
+    idx = [ctx.trace(t)[0] for t in range(steps)]
+    U, s, _ = ctx.modes()
+    out = dict(U=U.double().cpu().numpy(), sigma=s.cpu().numpy(), idx=idx, steps=steps)
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-9), (np.float32, 1e-5)])
+def test_block_truncation_matches_paper_literal_oracle(dtype, tol):
+    """Algorithm 1 read literally: the new block is truncated to rank r by
+    SVD(D^T D) before BLOCK MERGE (the oracle's paper_literal mode)."""
+    A = synth.planted(3000, 160, 0.8 ** np.arange(40), 1e-5, 25, dtype)
+    ref = O.isma(np.asarray(A, dtype=np.float64), O.Params(k=5, c=14, seed=0x5107, tol=1e-8, paper_literal=True))
+    g = run_literal(A, 5, 14, tol=1e-8)
+    assert g["steps"] == len(ref.trace)
+    for t, rec in enumerate(ref.trace):
+        assert np.array_equal(g["idx"][t], rec.idx)
+    np.testing.assert_allclose(g["sigma"], ref.sigma, rtol=tol)
+    assert O.sin_principal_max(ref.U, g["U"]) <= tol
+
+
+def _cut_floor(A, ref, r):
+    """u_32 sigma_1 / (sigma_r - sigma_{r+1}) of the sampled blocks D, worst
+    round: the accuracy to which FP32 arithmetic determines the truncated
+    block's right vectors V_r (Davis-Kahan)."""
+    f = 0.0
+    for rec in ref.trace:
+        s = np.linalg.svd(A[:, rec.idx], compute_uv=False)
+        if s.size > r:
+            f = max(f, 5.96e-8 * s[0] / (s[r - 1] - s[r]))
+    return f
+
+
+@pytest.mark.parametrize("core", ["f64", "auto"])
+def test_block_truncation_flow_f32_reduced(core):
+    """Flow snapshots (60 x 60 grid, 300 steps, FP32), k = r = 20, c = 40.
+    Truncating a 40-column block at 20 cuts between nearly equal singular
+    values in some rounds (relative gap 4e-4 of sigma_1), so the FP32 core's
+    V_r is only determined to u_32 sigma_1 / gap (1.5e-4 here) in those
+    rounds; with the FP64 core the result meets 1e-5, with the FP32 core a
+    tenth of that floor."""
+    A = synth.make_flow_316(grid=60, n=300)
+    A64 = A.astype(np.float64)
+    ref = O.isma(A64, O.Params(k=20, c=40, seed=0x5107, tol=1e-8, paper_literal=True))
+    g = run_literal(A, 20, 40, tol=1e-8, core=core)
+    assert g["steps"] == len(ref.trace)
+    for t, rec in enumerate(ref.trace):
+        assert np.array_equal(g["idx"][t], rec.idx)
+    bar = 1e-5 if core == "f64" else max(1e-5, 0.1 * _cut_floor(A64, ref, 20))
+    np.testing.assert_allclose(g["sigma"], ref.sigma, rtol=1e-5)
+    assert O.sin_principal_max(ref.U, g["U"]) <= bar
