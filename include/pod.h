@@ -60,7 +60,14 @@ enum { POD_SUBSPACE = 0, POD_MODES = 1 };
 /* arithmetic of the core SVD of E (Algorithm 2):
  * POD_CORE_AUTO = FP64 for POD_F64 data, FP32 for POD_F32 data */
 enum { POD_CORE_AUTO = 0, POD_CORE_F32 = 1, POD_CORE_F64 = 2 };
-/* arithmetic of the tall projections (P = U^T C, Grams, updates) */
+/* arithmetic of the dense contractions:
+ * POD_PREC_F32    FP32 SIMT products, FP64 sums of FP32 partials
+ * POD_PREC_TF32X3 A^T U (refinement, ORT) on the tcgen05 tensor cores with
+ *                 split-TF32 products (x = hi + lo, three TF32 products;
+ *                 FP32-level accuracy), FP32 accumulation per 64 rows,
+ *                 double-float across; FP32 data, m and lda multiples of 4,
+ *                 r <= 64
+ * POD_PREC_BF16, POD_PREC_BF16X3: not in this build (POD_EUNSUPPORTED) */
 enum { POD_PREC_F32 = 0, POD_PREC_BF16 = 1, POD_PREC_BF16X3 = 2, POD_PREC_TF32X3 = 3 };
 
 /*
@@ -92,9 +99,9 @@ typedef struct pod_params {
     int32_t block_trunc;   /* 1: GET UPDATE truncates the new block to rank r
                               through SVD(D^T D) before the merge (the paper's
                               literal Algorithm 1); 0: D merges directly     */
-    int32_t precision;     /* POD_PREC_F32 (the only arithmetic of the
-                              projections in this build; others are
-                              POD_EUNSUPPORTED)                              */
+    int32_t precision;     /* POD_PREC_F32 | POD_PREC_TF32X3 (see above);
+                              TF32X3 with an unsupported shape, and the BF16
+                              forms, are POD_EUNSUPPORTED                    */
     int32_t keep_tape;     /* reserved for pod_backward; must be 0           */
     int32_t reserved;      /* must be 0                                      */
 } pod_params;
@@ -268,6 +275,21 @@ POD_API const char *pod_strerror(pod_status s);
  */
 POD_API pod_status pod_colnorms(const void *A_dev, int32_t dtype, int64_t m, int64_t n,
                         int64_t lda, double *s_dev, void *stream);
+
+/*
+ * pod_atu -- Y = A^T U, the dense contraction of the closing refinement
+ * (Algorithm 1, QR(A^T U)) and of the ORT weights (Eq. 6), as a step.
+ *   A_dev : device, m x n column-major (lda), dtype.
+ *   U_dev : device, m x r column-major (ld m), dtype.
+ *   Y_dev : device, n x r FP64 column-major (ld n), overwritten.
+ *   precision : POD_PREC_F32 (FP32 SIMT / FP64 SIMT for FP64 data) or
+ *               POD_PREC_TF32X3 (tcgen05, FP32 data, m and lda multiples of
+ *               4, 16-byte aligned A and U, r <= 64; else POD_EUNSUPPORTED).
+ * Allocates its workspace for the call; synchronises the stream.
+ * Errors: POD_EINVAL, POD_EUNSUPPORTED, POD_ENOMEM, POD_ECUDA, POD_ETIMEOUT.
+ */
+POD_API pod_status pod_atu(const void *A_dev, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                           const void *U_dev, int32_t r, double *Y_dev, int32_t precision, void *stream);
 
 /*
  * pod_sample -- draw c column indices with replacement with probability

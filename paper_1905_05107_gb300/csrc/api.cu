@@ -120,6 +120,11 @@ struct pod_ctx {
     unsigned *r_cnt, *counters_w;
     int32_t *r_rows, *r_rcnt, *r_h;
     void *Cbuf;
+    // A^T U on tensor cores (precision POD_PREC_TF32X3)
+    int use_tc;
+    AtuTcPlan tcplan;
+    double *tc_part;
+    unsigned *tc_counters;
     // host
     DevState *hstate;   // pinned mirror
     cudaGraphExec_t graph;
@@ -150,7 +155,8 @@ static void ctx_free(pod_ctx *c) {
                     c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
-                    c->r_rcnt, c->r_h, c->Cbuf, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX};
+                    c->r_rcnt, c->r_h, c->Cbuf, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
+                    c->tc_part, c->tc_counters};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->hstate) cudaFreeHost(c->hstate);
@@ -174,7 +180,8 @@ static pod_status check_params(const pod_params *p) {
     if (p->w < 0) return POD_EINVAL;
     if (p->block_trunc != 0 && p->block_trunc != 1) return POD_EINVAL;
     if (p->precision < POD_PREC_F32 || p->precision > POD_PREC_TF32X3) return POD_EINVAL;
-    if (p->precision != POD_PREC_F32 || p->keep_tape != 0) return POD_EUNSUPPORTED;
+    if ((p->precision != POD_PREC_F32 && p->precision != POD_PREC_TF32X3) || p->keep_tape != 0)
+        return POD_EUNSUPPORTED;
     if (p->reserved != 0) return POD_EINVAL;
     if (p->c > 256 || (p->r > 0 ? p->r : p->k) > 256) return POD_EUNSUPPORTED;
     if (!(p->tol == p->tol)) return POD_EINVAL;
@@ -244,6 +251,41 @@ static SmallArgs small_args(pod_ctx *c) {
     return s;
 }
 
+// Y = A^T U (n x r_cur of state st): split-TF32 tensor cores when the
+// context runs at POD_PREC_TF32X3, FP32 SIMT otherwise.
+template <typename T>
+static pod_status enqueue_atu(pod_ctx *c, const DevState *st, const uint8_t *mask, cudaStream_t s) {
+    if (c->use_tc) {
+        AtuTcArgs ta{};
+        ta.m = c->p.m;
+        ta.n = c->p.n;
+        ta.lda = c->p.lda;
+        ta.rmax = c->rmax;
+        ta.st = st;
+        ta.part = c->tc_part;
+        ta.Y = c->Y;
+        ta.counters = c->tc_counters;
+        ta.err = &c->st->status;
+        return launch_atu_tc(ta, c->tcplan, (const float *)c->A, (const float *)c->U, s);
+    }
+    AtuArgs<T> aa{};
+    aa.m = c->p.m;
+    aa.n = c->p.n;
+    aa.A = (const T *)c->A;
+    aa.lda = c->p.lda;
+    aa.U = (const T *)c->U;
+    aa.ldu = c->p.m;
+    aa.st = st;
+    aa.mask = mask;
+    aa.ldy = (int)c->p.n;
+    aa.rmax = c->rmax;
+    aa.part = c->part_atu;
+    aa.Y = c->Y;
+    aa.counters = c->atu_counters;
+    aa.vec = c->vec;
+    return launch_atu<T>(aa, c->aplan, s);
+}
+
 // One round of Algorithm 1 (probabilities, draws, GET UPDATE, BLOCK MERGE,
 // convergence test) as a fixed launch sequence.
 template <typename T>
@@ -251,22 +293,7 @@ static pod_status enqueue_round(pod_ctx *c) {
     cudaStream_t s = c->stream;
     const int64_t sPG = (int64_t)c->rmax * c->cmax + (int64_t)c->cmax * c->cmax;
     if (c->p.col_strategy == POD_ORT) {
-        AtuArgs<T> aa{};
-        aa.m = c->p.m;
-        aa.n = c->p.n;
-        aa.A = (const T *)c->A;
-        aa.lda = c->p.lda;
-        aa.U = (const T *)c->U;
-        aa.ldu = c->p.m;
-        aa.st = c->st;
-        aa.mask = c->mask;
-        aa.ldy = (int)c->p.n;
-        aa.rmax = c->rmax;
-        aa.part = c->part_atu;
-        aa.Y = c->Y;
-        aa.counters = c->atu_counters;
-        aa.vec = c->vec;
-        POD_TRY(launch_atu<T>(aa, c->aplan, s));
+        POD_TRY(enqueue_atu<T>(c, c->st, c->mask, s));
         mark(c);
         POD_TRY(launch_ort_values(c->s, c->Y, c->p.n, (int)c->p.n, c->st, c->mask, c->ort, s));
         mark(c);
@@ -452,22 +479,7 @@ static pod_status run_refine(pod_ctx *c) {
     // Y = A^T U
     k_set_state<<<1, 32, 0, s>>>(c->aux + 0, r, 0, 0, 1, 1);
     c->launches += 1;
-    AtuArgs<T> aa{};
-    aa.m = m;
-    aa.n = n;
-    aa.A = (const T *)c->A;
-    aa.lda = c->p.lda;
-    aa.U = (const T *)c->U;
-    aa.ldu = m;
-    aa.st = c->aux + 0;
-    aa.mask = nullptr;
-    aa.ldy = (int)n;
-    aa.rmax = c->rmax;
-    aa.part = c->part_atu;
-    aa.Y = c->Y;
-    aa.counters = c->atu_counters;
-    aa.vec = c->vec;
-    POD_TRY(launch_atu<T>(aa, c->aplan, s));
+    POD_TRY(enqueue_atu<T>(c, c->aux + 0, nullptr, s));
     c->launches += 1;
     // G = Y^T Y, CholeskyQR2 on the n x r matrix Y (FP64 tall passes)
     TallPlan yplan = tall_plan(POD_F64, n, r, r, c->sms);
@@ -610,6 +622,14 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     } else if (p->block_trunc) {
         c->gplan = row_gram_plan(p->dtype, p->m, c->cmax, c->sms);
     }
+    if (p->precision == POD_PREC_TF32X3) {
+        if (!atu_tc_supported(p->dtype, p->m, p->lda, c->rmax, A_dev, A_dev)) {
+            free(c);
+            return POD_EUNSUPPORTED;
+        }
+        c->use_tc = 1;
+        c->tcplan = atu_tc_plan(p->m, p->n, c->rmax, c->sms);
+    }
     if ((p->rows || p->block_trunc) && rows_small_smem(c->cmax) > 220 * 1024) {
         free(c);
         return POD_EUNSUPPORTED;
@@ -681,6 +701,10 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         ALLOC(c->r_rscale, c->wdraws);
         ALLOC(c->r_h, 1);
     }
+    if (c->use_tc) {
+        ALLOC(c->tc_part, c->tcplan.part_doubles);
+        ALLOC(c->tc_counters, c->tcplan.mtiles);
+    }
     if (p->rows || p->block_trunc) {
         unsigned char *Cb = nullptr;
         ALLOC(Cb, (size_t)m * rm * es);
@@ -724,6 +748,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     }
     if (p->rows || p->block_trunc)
         if (e == cudaSuccess) e = cudaMemsetAsync(c->counters_w, 0, (c->gplan.groups + 1) * sizeof(unsigned), s);
+    if (c->use_tc && e == cudaSuccess) e = cudaMemsetAsync(c->tc_counters, 0, c->tcplan.mtiles * sizeof(unsigned), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ctx_free(c);
@@ -800,8 +825,10 @@ pod_status pod_modes(pod_ctx *c, void *U_dev, double *sigma_dev, void *V_dev) {
     }
     if (c->p.refine && !c->refined) {
         st = c->p.dtype == POD_F32 ? run_refine<float>(c) : run_refine<double>(c);
+        if (st == POD_OK) st = read_state(c);
+        if (st == POD_OK && c->hstate->status != 0) st = (pod_status)c->hstate->status;
         if (st != POD_OK) {
-            if (st == POD_ECUDA) c->poisoned = true;
+            if (st == POD_ECUDA || st == POD_ETIMEOUT) c->poisoned = true;
             return st;
         }
     }
@@ -1073,6 +1100,98 @@ pod_status pod_colnorms(const void *A_dev, int32_t dtype, int64_t m, int64_t n, 
     if (!A_dev || !s_dev || m <= 0 || n <= 0 || lda < m) return POD_EINVAL;
     if (dtype != POD_F32 && dtype != POD_F64) return POD_EINVAL;
     return launch_colnorms(A_dev, dtype, m, n, lda, s_dev, (cudaStream_t)stream);
+}
+
+pod_status pod_atu(const void *A_dev, int32_t dtype, int64_t m, int64_t n, int64_t lda, const void *U_dev, int32_t r,
+                   double *Y_dev, int32_t precision, void *stream) {
+    if (!A_dev || !U_dev || !Y_dev || m <= 0 || n <= 0 || lda < m || r <= 0) return POD_EINVAL;
+    if (dtype != POD_F32 && dtype != POD_F64) return POD_EINVAL;
+    if (precision != POD_PREC_F32 && precision != POD_PREC_TF32X3) return POD_EUNSUPPORTED;
+    const bool tc = precision == POD_PREC_TF32X3;
+    if (tc && !atu_tc_supported(dtype, m, lda, r, A_dev, U_dev)) return POD_EUNSUPPORTED;
+    if (!tc && r > 256) return POD_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sms = device_sms();
+    DevState *stt = nullptr;
+    double *part = nullptr;
+    unsigned *cnt = nullptr;
+    pod_status st = dalloc(&stt, 1);
+    AtuTcPlan tp{};
+    AtuPlan ap{};
+    size_t ncnt = 0;
+    if (tc) {
+        tp = atu_tc_plan(m, n, r, sms);
+        if (st == POD_OK) st = dalloc(&part, tp.part_doubles);
+        ncnt = (size_t)tp.mtiles;
+    } else {
+        ap = atu_plan(dtype, m, n, r, sms);
+        if (st == POD_OK) st = dalloc(&part, (size_t)ap.split * n * r);
+        ncnt = (size_t)ap.grid.x + 64;
+    }
+    if (st == POD_OK) st = dalloc(&cnt, ncnt);
+    if (st == POD_OK && cudaMemsetAsync(cnt, 0, ncnt * sizeof(unsigned), s) != cudaSuccess) st = POD_ECUDA;
+    if (st == POD_OK) {
+        k_set_state<<<1, 32, 0, s>>>(stt, r, 0, 0, 0, 1);
+        if (tc) {
+            AtuTcArgs ta{};
+            ta.m = m;
+            ta.n = n;
+            ta.lda = lda;
+            ta.rmax = r;
+            ta.st = stt;
+            ta.part = part;
+            ta.Y = Y_dev;
+            ta.counters = cnt;
+            ta.err = &stt->status;
+            st = launch_atu_tc(ta, tp, (const float *)A_dev, (const float *)U_dev, s);
+        } else if (dtype == POD_F32) {
+            AtuArgs<float> aa{};
+            aa.m = m;
+            aa.n = n;
+            aa.A = (const float *)A_dev;
+            aa.lda = lda;
+            aa.U = (const float *)U_dev;
+            aa.ldu = m;
+            aa.st = stt;
+            aa.ldy = (int)n;
+            aa.rmax = r;
+            aa.part = part;
+            aa.Y = Y_dev;
+            aa.counters = cnt;
+            aa.vec = ((uintptr_t)A_dev % 16 == 0) && ((uintptr_t)U_dev % 16 == 0) && ((lda * 4) % 16 == 0) &&
+                     ((m * 4) % 16 == 0);
+            st = launch_atu<float>(aa, ap, s);
+        } else {
+            AtuArgs<double> aa{};
+            aa.m = m;
+            aa.n = n;
+            aa.A = (const double *)A_dev;
+            aa.lda = lda;
+            aa.U = (const double *)U_dev;
+            aa.ldu = m;
+            aa.st = stt;
+            aa.ldy = (int)n;
+            aa.rmax = r;
+            aa.part = part;
+            aa.Y = Y_dev;
+            aa.counters = cnt;
+            aa.vec = ((uintptr_t)A_dev % 16 == 0) && ((uintptr_t)U_dev % 16 == 0) && ((lda * 8) % 16 == 0) &&
+                     ((m * 8) % 16 == 0);
+            st = launch_atu<double>(aa, ap, s);
+        }
+    }
+    int status = 0;
+    if (st == POD_OK && (cudaMemcpyAsync(&status, &stt->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                         cudaStreamSynchronize(s) != cudaSuccess)) {
+        cudaGetLastError();
+        st = POD_ECUDA;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(stt);
+    cudaFree(part);
+    cudaFree(cnt);
+    if (st == POD_OK && status != 0) st = (pod_status)status;
+    return st;
 }
 
 pod_status pod_sample(const uint64_t *w_dev, uint8_t *mask_dev, int64_t n, int32_t c, uint64_t seed, int32_t t,

@@ -159,6 +159,25 @@ template <typename T>
 pod_status launch_row_gram(const RowArgs<T> &a, cudaStream_t s);
 int row_blocks(int64_t m);
 
+// ---------------------------------------------------------------- atu_tc.cu
+// Y = A^T U on tcgen05 tensor cores with split-TF32 products (FP32 data).
+struct AtuTcArgs {
+    int64_t m, n, lda;
+    int rmax;
+    const DevState *st;     // r = st->r_cur
+    double *part;           // mtiles x splits x 128 x nt
+    double *Y;              // n x r, ld n
+    unsigned *counters;     // one per M-tile, zero between launches
+    int *err;               // set to POD_ETIMEOUT when a bounded wait expires
+};
+struct AtuTcPlan {
+    int nt, mtiles, splits;
+    size_t smem, part_doubles;
+};
+int atu_tc_supported(int dtype, int64_t m, int64_t lda, int rmax, const void *A, const void *U);
+AtuTcPlan atu_tc_plan(int64_t m, int64_t n, int rmax, int sms);
+pod_status launch_atu_tc(const AtuTcArgs &a, const AtuTcPlan &plan, const float *A, const float *U, cudaStream_t s);
+
 // ------------------------------------------------------------------ wedin.cu
 // Eq. 7 residual norms after the refinement (see wedin.cu).
 struct WedinArgs {

@@ -30,7 +30,7 @@ POD_PREC_F32, POD_PREC_BF16, POD_PREC_BF16X3, POD_PREC_TF32X3 = 0, 1, 2, 3
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
             "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
-            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin"]
+            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu"]
 
 ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "core_svd", "update", "finish"]
 ORT_KERNELS = ["ort_atu", "ort_values"]
@@ -133,6 +133,7 @@ _STRATEGY = {"l2n": POD_L2N, "unf": POD_UNF, "ort": POD_ORT}
 _CRITERION = {"subspace": POD_SUBSPACE, "modes": POD_MODES}
 _CORE = {"auto": POD_CORE_AUTO, "f32": POD_CORE_F32, "f64": POD_CORE_F64}
 _ROW_STRATEGY = {"l2n": POD_ROW_L2N, "ls": POD_ROW_LS}
+_PRECISION = {"f32": POD_PREC_F32, "bf16": POD_PREC_BF16, "bf16x3": POD_PREC_BF16X3, "tf32x3": POD_PREC_TF32X3}
 
 
 @dataclass
@@ -151,7 +152,8 @@ class Context:
     def __init__(self, A, k: int, c: int, r: int = 0, col_strategy: str = "unf",
                  criterion: str = "subspace", tol: float = 1e-8, max_iter: int = 0,
                  refine: bool = True, seed: int = 0x5107, core: str = "auto", rows: bool = False,
-                 row_strategy: str = "l2n", w: int = 0, block_trunc: bool = False, stream=None):
+                 row_strategy: str = "l2n", w: int = 0, block_trunc: bool = False, precision: str = "f32",
+                 stream=None):
         import torch
         _check_colmajor(A)
         self.A = A                    # keeps the borrowed buffer alive
@@ -175,6 +177,7 @@ class Context:
         p.core = _CORE[core]
         p.seed = int(seed) & ((1 << 64) - 1)
         p.block_trunc = 1 if block_trunc else 0
+        p.precision = _PRECISION[precision]
         self.params = p
         self._h = ctypes.c_void_p()
         with torch.cuda.device(A.device):
@@ -302,6 +305,21 @@ def colnorms(A, stream=None):
     _check(lib().pod_colnorms(_ptr(A), _dtype_code(A), A.shape[0], A.shape[1], A.stride(1), _ptr(s),
                               _stream(stream)), "pod_colnorms")
     return s
+
+
+def atu(A, U, precision: str = "f32", stream=None):
+    """Y = A^T U (FP64, n x r) through pod_atu."""
+    import torch
+    _check_colmajor(A)
+    _check_colmajor(U)
+    if U.stride(1) != A.shape[0] or U.dtype != A.dtype:
+        raise ValueError("U must be m x r with leading dimension m and the dtype of A")
+    n, r = int(A.shape[1]), int(U.shape[1])
+    Y = torch.empty((r, n), dtype=torch.float64, device=A.device).t()
+    st = stream if stream is not None else torch.cuda.current_stream(A.device)
+    _check(lib().pod_atu(_ptr(A), _dtype_code(A), int(A.shape[0]), n, int(A.stride(1)), _ptr(U), r, _ptr(Y),
+                         _PRECISION[precision], _stream(st)), "pod_atu")
+    return Y
 
 
 def sample(w, mask, c: int, seed: int, t: int, stream_id: int = 0, stream=None):
