@@ -411,6 +411,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "m": int(m), "n": int(n), "k": K_MODES, "c": C_DRAWS,
                            "tol": TOL, "rounds": rounds, "strategy": "L2N round 0, UNF after",
                            "parallelism": "replicas" if world > 1 else "single GPU",
+                           "contractions": "A^T U on tcgen05 tensor cores, split-TF32 (3 products)",
                            "l2": "A is 0.80 GB, larger than the 129 MB L2: no flush between steps"},
                 "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(m * n * es),
                         "d2h_bytes_per_step": int(m * K_MODES * 4 + K_MODES * 8)},

@@ -152,7 +152,7 @@ class Context:
     def __init__(self, A, k: int, c: int, r: int = 0, col_strategy: str = "unf",
                  criterion: str = "subspace", tol: float = 1e-8, max_iter: int = 0,
                  refine: bool = True, seed: int = 0x5107, core: str = "auto", rows: bool = False,
-                 row_strategy: str = "l2n", w: int = 0, block_trunc: bool = False, precision: str = "f32",
+                 row_strategy: str = "l2n", w: int = 0, block_trunc: bool = False, precision: str = "auto",
                  stream=None):
         import torch
         _check_colmajor(A)
@@ -177,6 +177,13 @@ class Context:
         p.core = _CORE[core]
         p.seed = int(seed) & ((1 << 64) - 1)
         p.block_trunc = 1 if block_trunc else 0
+        if precision == "auto":
+            # FP32 data: the A^T U contractions on tensor cores (split TF32)
+            # wherever the layout allows it
+            rr = int(r) if int(r) > 0 else int(k)
+            ok = (A.dtype == torch.float32 and self.m % 4 == 0 and int(A.stride(1)) % 4 == 0 and rr <= 64
+                  and A.data_ptr() % 16 == 0)
+            precision = "tf32x3" if ok else "f32"
         p.precision = _PRECISION[precision]
         self.params = p
         self._h = ctypes.c_void_p()
