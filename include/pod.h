@@ -102,7 +102,11 @@ typedef struct pod_params {
     int32_t precision;     /* POD_PREC_F32 | POD_PREC_TF32X3 (see above);
                               TF32X3 with an unsupported shape, and the BF16
                               forms, are POD_EUNSUPPORTED                    */
-    int32_t keep_tape;     /* reserved for pod_backward; must be 0           */
+    int32_t keep_tape;     /* 1: record, per round, the basis U_t entering
+                              the merge and the merge core (E, its singular
+                              values and left vectors, Ptot, R^{-1}) so that
+                              pod_backward can run; O(T m r) device memory,
+                              grown between batches of rounds; ICS only     */
     int32_t reserved;      /* must be 0                                      */
 } pod_params;
 
@@ -210,9 +214,23 @@ POD_API pod_status pod_replay_indices(pod_ctx *ctx, const int32_t *idx_host,
                               const int32_t *offsets_host, int32_t T);
 
 /*
- * pod_backward -- adjoint of the truncated POD of a finished run: given
- * dL/dU (m x k) and dL/dsigma (k), accumulate dL/dA into dA (m x n, ld lda).
- * Returns POD_EUNSUPPORTED in this build.
+ * pod_backward -- adjoint of the truncated POD of a finished run, with the
+ * run's draws held fixed (the draws are discrete; the derivative is that of
+ * the map A -> (U, sigma) for those index sets).  Given dL/dU and dL/dsigma
+ * of the k returned modes (pod_modes' outputs, signs included), computes
+ * dL/dA: reverse-mode through the closing refinement (the SVD of U^T A) and
+ * every merge of Algorithm 2 (the SVD of [U Sigma, D], Eqs. 8-9) using the
+ * SVD adjoint with the 1 / (sigma_j^2 - sigma_i^2) coupling (broadened:
+ * d / (d^2 + (1e-12 sigma_1^2)^2)), the sampled blocks D re-gathered from A by
+ * the recorded indices.
+ *   dU_dev     : device, m x k, ld m, dtype.
+ *   dsigma_dev : device, k doubles, or NULL (zero).
+ *   dA_dev     : device, m x n, ld lda, dtype; overwritten (accumulate = 0)
+ *                or added to (accumulate = 1).
+ * Needs keep_tape = 1 (else POD_ESTATE) and pod_modes to have run.
+ * Allocates O(m r) workspace for the call; synchronises the stream.
+ * Errors: POD_EINVAL, POD_ESTATE, POD_EUNSUPPORTED (tape overflow), POD_ENOMEM,
+ * POD_ECUDA.
  */
 POD_API pod_status pod_backward(pod_ctx *ctx, const void *dU_dev, const double *dsigma_dev,
                         void *dA_dev, int32_t accumulate);

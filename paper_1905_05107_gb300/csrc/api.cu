@@ -120,6 +120,10 @@ struct pod_ctx {
     unsigned *r_cnt, *counters_w;
     int32_t *r_rows, *r_rcnt, *r_h;
     void *Cbuf;
+    // pod_backward tape (keep_tape = 1): host copy of the device TapePtrs
+    TapePtrs tape_h;
+    TapePtrs *tape_d;
+    bool modes_done;
     // A^T U on tensor cores (precision POD_PREC_TF32X3)
     int use_tc;
     AtuTcPlan tcplan;
@@ -159,6 +163,9 @@ static void ctx_free(pod_ctx *c) {
                     c->tc_part, c->tc_counters};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    if (c->tape_h.U) cudaFree(c->tape_h.U);
+    if (c->tape_h.core) cudaFree(c->tape_h.core);
+    if (c->tape_d) cudaFree(c->tape_d);
     if (c->hstate) cudaFreeHost(c->hstate);
     free(c);
 }
@@ -180,8 +187,9 @@ static pod_status check_params(const pod_params *p) {
     if (p->w < 0) return POD_EINVAL;
     if (p->block_trunc != 0 && p->block_trunc != 1) return POD_EINVAL;
     if (p->precision < POD_PREC_F32 || p->precision > POD_PREC_TF32X3) return POD_EINVAL;
-    if ((p->precision != POD_PREC_F32 && p->precision != POD_PREC_TF32X3) || p->keep_tape != 0)
-        return POD_EUNSUPPORTED;
+    if (p->keep_tape != 0 && p->keep_tape != 1) return POD_EINVAL;
+    if (p->precision != POD_PREC_F32 && p->precision != POD_PREC_TF32X3) return POD_EUNSUPPORTED;
+    if (p->keep_tape && (p->rows || p->block_trunc)) return POD_EUNSUPPORTED;
     if (p->reserved != 0) return POD_EINVAL;
     if (p->c > 256 || (p->r > 0 ? p->r : p->k) > 256) return POD_EUNSUPPORTED;
     if (!(p->tol == p->tol)) return POD_EINVAL;
@@ -251,6 +259,36 @@ static SmallArgs small_args(pod_ctx *c) {
     return s;
 }
 
+// Make the tape hold at least `slots` rounds (U_t and the merge record);
+// grows by doubling, keeping what was recorded.  Host side, between batches.
+static pod_status tape_reserve(pod_ctx *c, int slots) {
+    if (!c->p.keep_tape || slots <= c->tape_h.cap) return POD_OK;
+    int cap = c->tape_h.cap > 0 ? c->tape_h.cap : 4;
+    while (cap < slots) cap *= 2;
+    const size_t es = c->p.dtype == POD_F32 ? 4 : 8;
+    const size_t ubytes = (size_t)c->p.m * c->rmax * es;
+    const int64_t stride = tape_layout(c->rmax, c->cmax).stride;
+    void *U = nullptr;
+    double *core = nullptr;
+    if (cudaMalloc(&U, ubytes * cap) != cudaSuccess || cudaMalloc((void **)&core, (size_t)stride * cap * 8) != cudaSuccess) {
+        cudaGetLastError();
+        if (U) cudaFree(U);
+        return POD_ENOMEM;
+    }
+    cudaStream_t s = c->stream;
+    TapePtrs nt{U, core, cap};
+    if (c->tape_h.cap > 0) {
+        POD_CUDA_TRY(cudaMemcpyAsync(U, c->tape_h.U, ubytes * c->tape_h.cap, cudaMemcpyDeviceToDevice, s));
+        POD_CUDA_TRY(cudaMemcpyAsync(core, c->tape_h.core, (size_t)stride * c->tape_h.cap * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    POD_CUDA_TRY(cudaMemcpyAsync(c->tape_d, &nt, sizeof(TapePtrs), cudaMemcpyHostToDevice, s));
+    POD_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c->tape_h.U) cudaFree(c->tape_h.U);
+    if (c->tape_h.core) cudaFree(c->tape_h.core);
+    c->tape_h = nt;
+    return POD_OK;
+}
+
 // Y = A^T U (n x r_cur of state st): split-TF32 tensor cores when the
 // context runs at POD_PREC_TF32X3, FP32 SIMT otherwise.
 template <typename T>
@@ -291,6 +329,10 @@ static pod_status enqueue_atu(pod_ctx *c, const DevState *st, const uint8_t *mas
 template <typename T>
 static pod_status enqueue_round(pod_ctx *c) {
     cudaStream_t s = c->stream;
+    if (c->p.keep_tape) {
+        POD_TRY(launch_tape_u<T>(c->tape_d, c->st, (const T *)c->U, c->p.m, c->rmax, s));
+        mark(c);
+    }
     const int64_t sPG = (int64_t)c->rmax * c->cmax + (int64_t)c->cmax * c->cmax;
     if (c->p.col_strategy == POD_ORT) {
         POD_TRY(enqueue_atu<T>(c, c->st, c->mask, s));
@@ -415,6 +457,7 @@ static pod_status enqueue_round(pod_ctx *c) {
     POD_TRY(launch_tall<T>(TALL_CGS, ta, c->plan, s));
     mark(c);
     SmallArgs sm = small_args(c);
+    sm.tape = c->p.keep_tape ? c->tape_d : nullptr;
     POD_TRY(launch_small_chol(sm, s));
     mark(c);
     ta.part_stride = (int64_t)c->cmax * c->cmax;
@@ -476,6 +519,13 @@ static pod_status run_refine(pod_ctx *c) {
     const int r = c->hstate->r_cur;
     const int64_t m = c->p.m, n = c->p.n;
     if (r == 0) return POD_OK;
+    if (c->p.keep_tape) {
+        // U_T, the basis the refinement starts from, for pod_backward
+        const int T_ = c->hstate->rounds_run;
+        POD_TRY(tape_reserve(c, T_ + 1));
+        POD_CUDA_TRY(cudaMemcpyAsync((T *)c->tape_h.U + (int64_t)T_ * m * c->rmax, c->U, (size_t)m * r * sizeof(T),
+                                     cudaMemcpyDeviceToDevice, s));
+    }
     // Y = A^T U
     k_set_state<<<1, 32, 0, s>>>(c->aux + 0, r, 0, 0, 1, 1);
     c->launches += 1;
@@ -574,6 +624,190 @@ static pod_status write_modes(pod_ctx *c, void *U_dev, double *sigma_dev, void *
         c->launches += 1;
     }
     return POD_OK;
+}
+
+// Adjoint of the truncated POD with the draws of the forward run held fixed:
+// the refinement first (when it ran), then the merges in reverse order, each
+// as a Gram pass, a one-CTA coefficient kernel and a row-mix pass that writes
+// the next basis adjoint and adds the sampled columns' adjoint into dA.
+template <typename T>
+static pod_status run_backward(pod_ctx *c, const void *dU_dev, const double *dsigma_dev, void *dA_dev,
+                               int32_t accumulate) {
+    cudaStream_t s = c->stream;
+    POD_TRY(read_state(c));
+    const int T_ = c->hstate->rounds_run;
+    const int k = c->p.k, rmax = c->rmax, cmax = c->cmax, nmax = rmax + cmax;
+    const int64_t m = c->p.m, n = c->p.n, lda = c->p.lda;
+    const int rT = c->hstate->r_cur;
+    if (T_ + 1 > c->tape_h.cap) return POD_EUNSUPPORTED;
+    if (rT < 1) return POD_ESTATE;
+    const TapeLayout TL = tape_layout(rmax, cmax);
+    // per-round sizes from the tape
+    double *meta = (double *)malloc((size_t)(T_ > 0 ? T_ : 1) * 4 * sizeof(double));
+    if (!meta) return POD_ENOMEM;
+    if (T_ > 0 && cudaMemcpy2DAsync(meta, 4 * sizeof(double), c->tape_h.core, TL.stride * sizeof(double),
+                                    4 * sizeof(double), T_, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        cudaGetLastError();
+        free(meta);
+        return POD_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        free(meta);
+        return POD_ECUDA;
+    }
+    const int es = (int)sizeof(T);
+    const int maxcols = rmax + cmax + rmax;
+    BwdGramPlan gp = bwd_gram_plan(c->p.dtype, m, maxcols > rmax + k ? maxcols : rmax + k, c->sms);
+    T *GU[2] = {nullptr, nullptr}, *AY = nullptr, *Lref = nullptr;
+    double *G = nullptr, *part = nullptr, *gsum = nullptr, *coef = nullptr, *work = nullptr, *sb[2] = {nullptr, nullptr};
+    double *coefL = nullptr, *coefT = nullptr;
+    unsigned *cnt = nullptr;
+    const size_t gmax = (size_t)(rmax + cmax) * maxcols > (size_t)rmax * (rmax + k) ? (size_t)(rmax + cmax) * maxcols
+                                                                                   : (size_t)rmax * (rmax + k);
+    pod_status st = POD_OK;
+#define BALLOC(ptr, cnt_) if (st == POD_OK) st = dalloc(&(ptr), (size_t)(cnt_))
+    BALLOC(GU[0], (size_t)m * rmax);
+    BALLOC(GU[1], (size_t)m * rmax);
+    BALLOC(AY, (size_t)m * rmax);
+    BALLOC(Lref, (size_t)m * rmax);
+    BALLOC(G, gmax);
+    BALLOC(part, (size_t)gp.grid * gmax);
+    BALLOC(gsum, (size_t)(gp.groups + 1) * gmax);
+    BALLOC(coef, (size_t)maxcols * maxcols);
+    BALLOC(work, (size_t)6 * nmax * nmax + 2 * rmax * rmax);
+    BALLOC(sb[0], rmax > k ? rmax : k);
+    BALLOC(sb[1], rmax > k ? rmax : k);
+    BALLOC(coefL, (size_t)rmax * rmax);
+    BALLOC(coefT, (size_t)(k + rmax) * rmax);
+    BALLOC(cnt, gp.groups + 1);
+#undef BALLOC
+    if (st == POD_OK && cudaMemsetAsync(cnt, 0, (gp.groups + 1) * sizeof(unsigned), s) != cudaSuccess) st = POD_ECUDA;
+    auto gram = [&](const void *p0, int64_t ld0, const int32_t *i0, int n0, const void *p1, int64_t ld1,
+                    const int32_t *i1, int n1, const void *p2, int64_t ld2, int n2, int nleft) {
+        BwdGram ga{};
+        ga.ptr[0] = p0; ga.ld[0] = ld0; ga.idx[0] = i0; ga.ncol[0] = n0;
+        ga.ptr[1] = p1; ga.ld[1] = ld1; ga.idx[1] = i1; ga.ncol[1] = n1;
+        ga.ptr[2] = p2; ga.ld[2] = ld2; ga.idx[2] = nullptr; ga.ncol[2] = n2;
+        ga.nleft = nleft;
+        ga.m = m;
+        ga.rows_per = gp.rows_per;
+        ga.lds = gp.lds;
+        ga.part = part;
+        ga.gsum = gsum;
+        ga.out = G;
+        ga.counters = cnt;
+        c->launches += 1;
+        return launch_bwd_gram<T>(ga, gp, s);
+    };
+    const T *Ufin = (const T *)c->U;
+    // ------------------------------------------------ refinement
+    if (st == POD_OK) {
+        if (c->refined) {
+            const int r = c->refined_r;
+            st = gram(Ufin, m, nullptr, r, dU_dev, m, nullptr, k, nullptr, 0, 0, 1);
+            BwdRefine br{};
+            br.r = r;
+            br.k = k;
+            br.G = G;
+            br.ldg = r + k;
+            br.goff = r;
+            br.S = c->rsig;
+            br.VR = c->rVR;
+            br.K = c->rK;
+            br.dots = c->dots;
+            br.dsigma = dsigma_dev;
+            br.work = work;
+            br.coefL = coefL;
+            br.coefT = coefT;
+            if (st == POD_OK) st = launch_bwd_refine_small(br, s);
+            if (st == POD_OK) st = launch_az<T>((const T *)c->A, m, n, lda, c->Y, r, AY, s);
+            RowMix rm{};
+            rm.m = m;
+            rm.in[0] = Ufin; rm.ldi[0] = m; rm.pin[0] = r;
+            rm.out[0] = Lref; rm.ldo[0] = m; rm.qout[0] = r;
+            rm.coef = coefL;
+            if (st == POD_OK) st = launch_rowmix<T>(rm, s);
+            if (st == POD_OK) st = launch_outer<T>((T *)dA_dev, m, n, lda, Lref, r, c->Y, accumulate, s);
+            RowMix rt{};
+            rt.m = m;
+            rt.in[0] = dU_dev; rt.ldi[0] = m; rt.pin[0] = k;
+            rt.in[1] = AY; rt.ldi[1] = m; rt.pin[1] = r;
+            rt.out[0] = GU[0]; rt.ldo[0] = m; rt.qout[0] = r;
+            rt.coef = coefT;
+            if (st == POD_OK) st = launch_rowmix<T>(rt, s);
+            if (st == POD_OK && cudaMemsetAsync(sb[0], 0, rmax * sizeof(double), s) != cudaSuccess) st = POD_ECUDA;
+            c->launches += 5;
+        } else {
+            // U_fin = U_T: only the sign fix lies between the rounds and the output
+            double *hc = (double *)calloc((size_t)k * rT, sizeof(double));
+            double *hd = (double *)malloc((size_t)rT * sizeof(double));
+            double *hs = (double *)calloc((size_t)rT, sizeof(double));
+            if (!hc || !hd || !hs) st = POD_ENOMEM;
+            if (st == POD_OK && (cudaMemcpy(hd, c->dots, rT * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                                 (dsigma_dev && cudaMemcpy(hs, dsigma_dev, (k < rT ? k : rT) * sizeof(double),
+                                                           cudaMemcpyDeviceToHost) != cudaSuccess)))
+                st = POD_ECUDA;
+            if (st == POD_OK) {
+                for (int l = 0; l < k && l < rT; ++l) hc[l * rT + l] = hd[l] < 0.0 ? -1.0 : 1.0;
+                if (cudaMemcpy(coefT, hc, (size_t)k * rT * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+                    cudaMemcpy(sb[0], hs, rT * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+                    st = POD_ECUDA;
+            }
+            free(hc);
+            free(hd);
+            free(hs);
+            RowMix rt{};
+            rt.m = m;
+            rt.in[0] = dU_dev; rt.ldi[0] = m; rt.pin[0] = k;
+            rt.out[0] = GU[0]; rt.ldo[0] = m; rt.qout[0] = rT;
+            rt.coef = coefT;
+            if (st == POD_OK) st = launch_rowmix<T>(rt, s);
+            if (st == POD_OK && !accumulate &&
+                cudaMemset2DAsync(dA_dev, (size_t)lda * es, 0, (size_t)m * es, (size_t)n, s) != cudaSuccess)
+                st = POD_ECUDA;
+        }
+    }
+    // ------------------------------------------------ merges, last to first
+    int cur = 0;
+    for (int t = T_ - 1; t >= 0 && st == POD_OK; --t) {
+        const int r = (int)meta[4 * t + 0], g = (int)meta[4 * t + 1], rp = (int)meta[4 * t + 2];
+        const T *Ut = (const T *)c->tape_h.U + (int64_t)t * m * rmax;
+        const int32_t *idx = c->hist_idx + (int64_t)t * c->p.c;
+        st = gram(Ut, m, nullptr, r, c->A, lda, idx, g, GU[cur], m, rp, 2);
+        BwdMerge bm{};
+        bm.rec = c->tape_h.core + (int64_t)t * TL.stride;
+        bm.rmax = rmax;
+        bm.cmax = cmax;
+        bm.dtype = c->p.dtype;
+        bm.G = G;
+        bm.sbar = sb[cur];
+        bm.work = work;
+        bm.coef = coef;
+        bm.sbar_out = sb[cur ^ 1];
+        if (st == POD_OK) st = launch_bwd_merge_small(bm, s);
+        RowMix rm{};
+        rm.m = m;
+        rm.in[0] = Ut; rm.ldi[0] = m; rm.pin[0] = r;
+        rm.in[1] = c->A; rm.ldi[1] = lda; rm.idx_in[1] = idx; rm.pin[1] = g;
+        rm.in[2] = GU[cur]; rm.ldi[2] = m; rm.pin[2] = rp;
+        rm.out[0] = GU[cur ^ 1]; rm.ldo[0] = m; rm.qout[0] = r;
+        rm.out[1] = dA_dev; rm.ldo[1] = lda; rm.idx_out[1] = idx; rm.qout[1] = g; rm.acc_out[1] = 1;
+        rm.coef = coef;
+        if (st == POD_OK) st = launch_rowmix<T>(rm, s);
+        c->launches += 2;
+        cur ^= 1;
+    }
+    if (st == POD_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        st = POD_ECUDA;
+    }
+    cudaStreamSynchronize(s);
+    void *bufs[] = {GU[0], GU[1], AY, Lref, G, part, gsum, coef, work, sb[0], sb[1], coefL, coefT, cnt};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    free(meta);
+    return st;
 }
 
 extern "C" {
@@ -701,6 +935,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         ALLOC(c->r_rscale, c->wdraws);
         ALLOC(c->r_h, 1);
     }
+    if (p->keep_tape) ALLOC(c->tape_d, 1);
     if (c->use_tc) {
         ALLOC(c->tc_part, c->tcplan.part_doubles);
         ALLOC(c->tc_counters, c->tcplan.mtiles);
@@ -754,6 +989,20 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         ctx_free(c);
         return POD_ECUDA;
     }
+    if (p->keep_tape) {
+        const TapePtrs z{nullptr, nullptr, 0};
+        if (cudaMemcpy(c->tape_d, &z, sizeof(TapePtrs), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            ctx_free(c);
+            return POD_ECUDA;
+        }
+        const int64_t est = 2 * ((n + p->c - 1) / p->c) + 4;
+        pod_status ts = tape_reserve(c, (int)(est < n + 1 ? est : n + 1));
+        if (ts != POD_OK) {
+            ctx_free(c);
+            return ts;
+        }
+    }
     k_set_state<<<1, 32, 0, s>>>(c->st, 0, 0, 0, 0, (int)n);
     mark(c);
     pod_status ls = launch_colnorms(A_dev, p->dtype, m, n, p->lda, c->s, s);
@@ -783,6 +1032,10 @@ pod_status pod_iterate(pod_ctx *c, int32_t max_steps, int32_t *done, double *sin
         if (chunk < 1) chunk = 1;
         if (chunk > 64) chunk = 64;
         if (chunk > max_steps - launched) chunk = max_steps - launched;
+        if (c->p.keep_tape) {
+            st = tape_reserve(c, c->hstate->t + chunk + 1);
+            if (st != POD_OK) return st;
+        }
         for (int i = 0; i < chunk; ++i) {
             if (c->graph_ready) {
                 if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) {
@@ -835,6 +1088,7 @@ pod_status pod_modes(pod_ctx *c, void *U_dev, double *sigma_dev, void *V_dev) {
     st = c->p.dtype == POD_F32 ? write_modes<float>(c, U_dev, sigma_dev, V_dev)
                                : write_modes<double>(c, U_dev, sigma_dev, V_dev);
     if (st == POD_ECUDA) c->poisoned = true;
+    if (st == POD_OK) c->modes_done = true;
     return st;
 }
 
@@ -881,12 +1135,13 @@ pod_status pod_replay_indices(pod_ctx *c, const int32_t *idx_host, const int32_t
 
 pod_status pod_backward(pod_ctx *c, const void *dU_dev, const double *dsigma_dev, void *dA_dev,
                         int32_t accumulate) {
-    (void)dU_dev;
-    (void)dsigma_dev;
-    (void)dA_dev;
-    (void)accumulate;
-    if (!c) return POD_EINVAL;
-    return POD_EUNSUPPORTED;
+    if (!c || !dU_dev || !dA_dev) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (!c->p.keep_tape || !c->modes_done) return POD_ESTATE;
+    pod_status st = c->p.dtype == POD_F32 ? run_backward<float>(c, dU_dev, dsigma_dev, dA_dev, accumulate)
+                                          : run_backward<double>(c, dU_dev, dsigma_dev, dA_dev, accumulate);
+    if (st == POD_ECUDA) c->poisoned = true;
+    return st;
 }
 
 pod_status pod_last_rows(pod_ctx *c, int32_t *rows_host, int32_t *counts_host, int32_t cap, int32_t *h) {
@@ -1016,6 +1271,7 @@ static pod_status reset_state(pod_ctx *c) {
     c->hstate->remaining = (int)n;
     c->refined = false;
     c->refined_r = 0;
+    c->modes_done = false;
     return POD_OK;
 }
 

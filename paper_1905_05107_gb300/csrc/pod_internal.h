@@ -196,6 +196,97 @@ int wedin_passes(int k);
 template <typename T>
 pod_status launch_wedin(const WedinArgs &a, const T *A, const T *U, cudaStream_t s);
 
+// --------------------------------------------------------- backward tape
+// Where the forward records what pod_backward needs: the basis U_t entering
+// every round (m x rmax, storage type) and a per-round record of the merge
+// core.  Device-resident so the host can grow the buffers between batches of
+// rounds without re-capturing the round graph.
+struct TapePtrs {
+    void *U;        // cap slots of m * rmax elements
+    double *core;   // cap records of tape_layout(...).stride doubles
+    int cap;
+};
+// Record of round t (doubles): [0] r_t, [1] g_t, [2] r_new, [3] n_c; then
+// sig (nmax: all singular values of E, descending), E (nmax x nmax, column-
+// major, ld nmax), UE (nmax x nmax: left singular vector s at s * nmax),
+// Ptot (rmax x cmax, ld cmax), Rinv (cmax x cmax, ld cmax).
+struct TapeLayout {
+    int64_t sig, E, UE, Ptot, Rinv, stride;
+};
+__host__ __device__ inline TapeLayout tape_layout(int rmax, int cmax) {
+    const int64_t nmax = rmax + cmax;
+    TapeLayout L;
+    L.sig = 8;
+    L.E = L.sig + nmax;
+    L.UE = L.E + nmax * nmax;
+    L.Ptot = L.UE + nmax * nmax;
+    L.Rinv = L.Ptot + (int64_t)rmax * cmax;
+    L.stride = L.Rinv + (int64_t)cmax * cmax;
+    return L;
+}
+template <typename T>
+pod_status launch_tape_u(const TapePtrs *tp, const DevState *st, const T *U, int64_t m, int rmax, cudaStream_t s);
+
+// ---------------------------------------------------------- backward.cu
+struct BwdGram {            // G = [blocks < nleft]^T [blocks], row-major nl x nt
+    const void *ptr[3];
+    int64_t ld[3];
+    const int32_t *idx[3];  // column gather (or null)
+    int ncol[3];
+    int nleft;
+    int64_t m;
+    int rows_per, lds;
+    double *part, *gsum, *out;
+    unsigned *counters;     // groups + 1, zero between launches
+};
+struct BwdGramPlan {
+    int grid, rows_per, lds, groups;
+    size_t smem;
+};
+BwdGramPlan bwd_gram_plan(int dtype, int64_t m, int ncols, int sms);
+template <typename T>
+pod_status launch_bwd_gram(const BwdGram &a, const BwdGramPlan &p, cudaStream_t s);
+struct RowMix {             // out_o[i, q] (+)= sum_b in_b[i, :] coef[rows of b][cols of o]
+    int64_t m;
+    const void *in[3];
+    int64_t ldi[3];
+    const int32_t *idx_in[3];
+    int pin[3];
+    void *out[2];
+    int64_t ldo[2];
+    const int32_t *idx_out[2];
+    int qout[2];
+    int acc_out[2];
+    const double *coef;     // (sum pin) x (sum qout), row-major
+};
+template <typename T>
+pod_status launch_rowmix(const RowMix &a, cudaStream_t s);
+template <typename T>
+pod_status launch_az(const T *A, int64_t m, int64_t n, int64_t lda, const double *Y, int r, T *out, cudaStream_t s);
+template <typename T>
+pod_status launch_outer(T *dA, int64_t m, int64_t n, int64_t lda, const T *L, int r, const double *R, int acc,
+                        cudaStream_t s);
+struct BwdRefine {
+    int r, k;
+    const double *G;        // r x (r + k): U_fin^T [U_fin, Ubar_out]
+    int ldg, goff;
+    const double *S, *VR, *K, *dots, *dsigma;   // dsigma may be null
+    double *work;           // 2 r^2
+    double *coefL;          // r x r
+    double *coefT;          // (k + r) x r
+};
+pod_status launch_bwd_refine_small(const BwdRefine &a, cudaStream_t s);
+struct BwdMerge {
+    const double *rec;      // tape record of the round
+    int rmax, cmax, dtype;
+    const double *G;        // (r + g) x (r + g + r')
+    const double *sbar;     // r' incoming singular-value adjoints
+    double *work;           // 6 nmax^2
+    double *coef;           // (r + g + r') x (r + g)
+    double *sbar_out;       // r
+};
+pod_status launch_bwd_merge_small(const BwdMerge &a, cudaStream_t s);
+
 // ------------------------------------------------------------------ small.cu
 pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t count,
                          double *out, const DevState *st, cudaStream_t s);
@@ -217,6 +308,7 @@ struct SmallArgs {
     double *M1;             // g x g, ld cmax
     double *R1p;            // g x g, ld cmax
     double *E;              // nc x nc scratch (column-major, ld rmax + cmax)
+    const struct TapePtrs *tape;   // per-round merge record for pod_backward (or null)
     double *Xm;             // r x rn, ld rmax
     double *Ym;             // g x rn, ld rmax
     double *hist_measure;   // per-round measure

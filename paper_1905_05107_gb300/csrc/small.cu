@@ -15,7 +15,6 @@
 
 namespace {
 
-constexpr int SMALL_THREADS = 1024;
 // The one-CTA Cholesky kernels take a barrier per elimination step; with
 // O(n^2 / 4) work per step, 8 warps finish a step sooner than 32.
 constexpr int CHOL_THREADS = 256;
@@ -866,6 +865,34 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         __syncthreads();
     }
     clk[4] = clock64();
+    if (a.tape && a.tape->core && t < a.tape->cap) {
+        // merge record for the adjoint: sizes, every singular value and left
+        // vector of E (refined ones for the first rsel), E, Ptot, R^{-1}
+        const TapeLayout TL = tape_layout(a.rmax, a.cmax);
+        double *tp = a.tape->core + (int64_t)t * TL.stride;
+        if (tid == 0) {
+            tp[0] = r;
+            tp[1] = g;
+            tp[2] = rn;
+            tp[3] = nc;
+        }
+        for (int s = tid; s < nc; s += bd)
+            tp[TL.sig + s] = s < rsel ? XOps<X>::to(sig[s]) : sqrt((double)alpha[order[s]]);
+        for (int e = tid; e < nc * nc; e += bd) {
+            const int q = e / nc, p = e % nc;
+            tp[TL.E + (int64_t)q * nmax + p] = XOps<X>::to(Ex[q * nc + p]);
+            tp[TL.UE + (int64_t)q * nmax + p] =
+                q < rsel ? XOps<X>::to(Q[q * nc + p]) : (double)V[(size_t)order[q] * nc + p];
+        }
+        for (int e = tid; e < r * g; e += bd) {
+            const int l = e / g, j = e % g;
+            tp[TL.Ptot + l * ld + j] = XOps<X>::to(Ptx[l * ld + j]);
+        }
+        for (int e = tid; e < g * g; e += bd) {
+            const int i = e / g, j = e % g;
+            tp[TL.Rinv + i * ld + j] = XOps<X>::to(Rinv[i * ld + j]);
+        }
+    }
     // Y = Rinv U_E[r:, :rn] (g x rn), X = U_E[:r, :rn] - Ptot Y (r x rn)
     for (int e = tid; e < g * rn; e += bd) {
         const int j = e / rn, q = e % rn;

@@ -153,7 +153,7 @@ class Context:
                  criterion: str = "subspace", tol: float = 1e-8, max_iter: int = 0,
                  refine: bool = True, seed: int = 0x5107, core: str = "auto", rows: bool = False,
                  row_strategy: str = "l2n", w: int = 0, block_trunc: bool = False, precision: str = "auto",
-                 stream=None):
+                 keep_tape: bool = False, stream=None):
         import torch
         _check_colmajor(A)
         self.A = A                    # keeps the borrowed buffer alive
@@ -185,6 +185,7 @@ class Context:
                   and A.data_ptr() % 16 == 0)
             precision = "tf32x3" if ok else "f32"
         p.precision = _PRECISION[precision]
+        p.keep_tape = 1 if keep_tape else 0
         self.params = p
         self._h = ctypes.c_void_p()
         with torch.cuda.device(A.device):
@@ -239,7 +240,8 @@ class Context:
         buf = (ctypes.c_float * 32)()
         cnt = ctypes.c_int32(0)
         _check(lib().pod_round_timings(self._h, buf, 32, ctypes.byref(cnt)), "pod_round_timings")
-        names = (ORT_KERNELS if self.params.col_strategy == POD_ORT else []) + ROUND_KERNELS[:1] + \
+        names = (["tape_u"] if self.params.keep_tape else []) + \
+            (ORT_KERNELS if self.params.col_strategy == POD_ORT else []) + ROUND_KERNELS[:1] + \
             (ROW_KERNELS if self.params.rows else (ROW_KERNELS[1:] if self.params.block_trunc else [])) + \
             ROUND_KERNELS[1:]
         return dict(zip(names, [float(x) for x in buf[: cnt.value]]))
@@ -263,6 +265,24 @@ class Context:
         meas = ctypes.c_double(0.0)
         _check(lib().pod_get_trace(self._h, int(t), idx, ctypes.byref(g), ctypes.byref(meas)), "pod_get_trace")
         return np.array(idx[: g.value], dtype=np.int64), float(meas.value)
+
+    def backward(self, dU, dsigma=None, accumulate: bool = False, dA=None):
+        """dL/dA for the frozen draws of this run (pod_backward); needs
+        keep_tape=True and modes() to have run.  dU: (m, k) like modes()'s U;
+        dsigma: (k,) FP64 or None.  Returns dA (m, n), column-major, A's dtype."""
+        import torch
+        dU = dU.to(self.dtype)
+        if dU.stride(0) != 1 or dU.stride(1) != self.m:
+            dU = dU.t().contiguous().t()
+        if dA is None:
+            dA = torch.empty((self.n, self.m), dtype=self.dtype, device=self.device).t()
+            accumulate = False
+        ds = None
+        if dsigma is not None:
+            ds = dsigma.to(torch.float64).contiguous()
+        _check(lib().pod_backward(self._h, _ptr(dU), _ptr(ds) if ds is not None else None, _ptr(dA),
+                                  1 if accumulate else 0), "pod_backward")
+        return dA
 
     def wedin(self):
         """Eq. 7 measure after pod_modes with refinement: dict with the bound,
@@ -357,3 +377,36 @@ def block_merge(U1, s1, C, r: int, core: str = "auto", stream=None):
                                  _ptr(C), C.stride(1), g, int(r), _CORE[core], _ptr(U_out), _ptr(s_out),
                                  ctypes.byref(rn), _stream(stream)), "pod_block_merge")
     return U_out[:, : rn.value], s_out[: rn.value]
+
+
+def _autograd_function():
+    import torch
+
+    class PODFunction(torch.autograd.Function):
+        """(U, sigma) = top-k POD modes of A by ISMA; backward through
+        pod_backward with the forward's draws held fixed."""
+
+        @staticmethod
+        def forward(fctx, A, k, c, kwargs):
+            ctx = Context(A, k, c, keep_tape=True, **kwargs)
+            ctx.iterate()
+            U, s, _ = ctx.modes()
+            fctx.pod = ctx
+            return U, s
+
+        @staticmethod
+        def backward(fctx, gU, gs):
+            ctx = fctx.pod
+            if gU is None:
+                gU = torch.zeros((ctx.m, ctx.k), dtype=ctx.dtype, device=ctx.device)
+            dA = ctx.backward(gU, gs)
+            ctx.close()
+            return dA, None, None, None
+
+    return PODFunction
+
+
+def pod_modes_autograd(A, k: int, c: int, **kw):
+    """Differentiable (U, sigma) of A (torch.autograd)."""
+    return _autograd_function().apply(A, k, c, kw)
+

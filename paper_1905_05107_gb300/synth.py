@@ -155,3 +155,26 @@ def make_planted_small(seed: int = SEED_DATA + 1, dtype=np.float64) -> np.ndarra
 def make_flow_316(seed: int = SEED_DATA + 2, dtype=np.float32, grid: int = 316,
                   n: int = 2000) -> np.ndarray:
     return flow(grid, n, 60, 1e-3, seed, dtype)
+
+
+DIFF_C4 = Workload(
+    "planted-200000x1000-f32-diff", 200_000, 1000, 16, 32, np.float32, 1e-8,
+    "planted sigma_i = 1 - 0.05 (i - 1) for i = 1..16 (gaps 0.05), then "
+    "0.1 exp(-(i - 17) / 10) for i = 17..64; Haar U (200000x64), V (1000x64); "
+    "no noise, rows centred, FP32; k=16, c=32")
+
+
+def diff_sigma() -> np.ndarray:
+    i = np.arange(1, 65, dtype=np.float64)
+    return np.where(i <= 16, 1.0 - 0.05 * (i - 1), 0.1 * np.exp(-(i - 17) / 10.0))
+
+
+def make_diff_c4(seed: int = SEED_DATA + 4, dtype=np.float32, m: int = 200_000, n: int = 1000) -> np.ndarray:
+    """The differentiation workload (sizes reducible for quick cases)."""
+    return planted(m, n, diff_sigma(), 0.0, seed, dtype)
+
+
+def diff_loss_weights(k: int, m: int, seed: int = SEED_DATA + 40):
+    """Seeded w ~ U(0.5, 1.5)^k and g ~ N(0, I_m) of the loss sum w_i (u_i^T g)^2."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.5, 1.5, k), rng.standard_normal(m)
