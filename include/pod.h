@@ -326,6 +326,27 @@ POD_API pod_status pod_sample(const uint64_t *w_dev, uint8_t *mask_dev, int64_t 
                       int32_t *g_dev, void *stream);
 
 /*
+ * pod_incremental -- Algorithm 3 (incremental POD for matrices that do not
+ * fit in device memory): A is split into `blocks` column ranges
+ * [b n / t, (b + 1) n / t); each range is copied to the device on a side
+ * stream while the previous one is processed (two device buffers), ISMA
+ * (Algorithm 1 with p's parameters, r modes kept, no refinement) runs on it,
+ * and BLOCK MERGE (Algorithm 2) folds its r scaled modes into the running
+ * U, Sigma.  One pass over A.
+ *   p       : parameters (p->n, p->lda describe the whole host matrix;
+ *             keep_tape must be 0).
+ *   A_host  : host m x n column-major (lda), dtype; pinned memory lets the
+ *             copies overlap the computation.  Borrowed, read only.
+ *   U_dev   : device m x k (ld m), the first k modes with the sign
+ *             convention of pod_modes; sigma_dev : device k doubles.
+ * Allocates two m x ceil(n / t) device buffers and the per-block contexts
+ * for the call; synchronises the stream.
+ * Errors: as pod_init and pod_iterate; POD_EINVAL for blocks < 1 or > n.
+ */
+POD_API pod_status pod_incremental(const pod_params *p, const void *A_host, int32_t blocks, void *U_dev,
+                                   double *sigma_dev, void *stream);
+
+/*
  * pod_block_merge -- Algorithm 2 (BLOCK MERGE) with the new block given as
  * its scaled left factor C = U_2 Sigma_2 (m x g):
  * U_t = C - U_1 (U_1^T C) (computed twice), U_t = U_o R (CholeskyQR2),

@@ -64,6 +64,16 @@ __global__ void k_set_state(DevState *st, int r_cur, int g, int r_new, int t, in
     }
 }
 
+// C = U diag(sigma): the scaled left factor of a block (Algorithm 3's merge input)
+template <typename T>
+__global__ void k_scale_cols(const T *U, int64_t m, int r, const double *sigma, T *C) {
+    const int64_t total = m * r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e / m);
+        C[e] = (T)((double)U[e] * sigma[l]);
+    }
+}
+
 int device_sms() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -1485,6 +1495,165 @@ pod_status pod_sample(const uint64_t *w_dev, uint8_t *mask_dev, int64_t n, int32
     cudaFreeAsync(cdf, s);
     cudaFreeAsync(flags, s);
     cudaFreeAsync(draws, s);
+    return st;
+}
+
+pod_status pod_incremental(const pod_params *p, const void *A_host, int32_t blocks, void *U_dev, double *sigma_dev,
+                           void *stream) {
+    POD_TRY(check_params(p));
+    if (!A_host || !U_dev || !sigma_dev || blocks < 1 || blocks > p->n) return POD_EINVAL;
+    if (p->keep_tape) return POD_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t m = p->m, n = p->n;
+    const size_t es = p->dtype == POD_F32 ? 4 : 8;
+    const int r = p->r > 0 ? p->r : p->k;
+    const int64_t ldb = (m + 3) & ~(int64_t)3;   // 16-byte column starts
+    int64_t maxw = 0;
+    for (int b = 0; b < blocks; ++b) {
+        const int64_t w = (b + 1) * n / blocks - b * n / blocks;
+        maxw = w > maxw ? w : maxw;
+    }
+    void *buf[2] = {nullptr, nullptr}, *Cb = nullptr, *Ua[2] = {nullptr, nullptr};
+    double *sa[2] = {nullptr, nullptr}, *dots = nullptr, *part = nullptr;
+    pod_ctx *cache[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t cache_w[2][2] = {{0, 0}, {0, 0}};
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    pod_status st = POD_OK;
+    const int sms = device_sms();
+    const int sgrid = 2 * sms;
+    auto dalloc_bytes = [&](void **q, size_t bytes) {
+        if (st == POD_OK && cudaMalloc(q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st = POD_ENOMEM;
+        }
+    };
+    dalloc_bytes(&buf[0], (size_t)ldb * maxw * es);
+    dalloc_bytes(&buf[1], (size_t)ldb * maxw * es);
+    dalloc_bytes(&Cb, (size_t)m * r * es);
+    dalloc_bytes(&Ua[0], (size_t)m * r * es);
+    dalloc_bytes(&Ua[1], (size_t)m * r * es);
+    if (st == POD_OK) st = dalloc(&sa[0], r);
+    if (st == POD_OK) st = dalloc(&sa[1], r);
+    if (st == POD_OK) st = dalloc(&dots, r);
+    if (st == POD_OK) st = dalloc(&part, (size_t)sgrid * r);
+    if (st == POD_OK && (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&ev_copied[0], cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&ev_copied[1], cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&ev_free[0], cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&ev_free[1], cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        st = POD_ECUDA;
+    }
+    // copy of block b (host columns [b n / t, (b + 1) n / t)) into buf[b % 2]
+    auto copy_block = [&](int b) {
+        if (st != POD_OK) return;
+        const int64_t j0 = b * n / blocks, w = (b + 1) * n / blocks - j0;
+        const int q = b & 1;
+        if (b >= 2 && cudaStreamWaitEvent(cs, ev_free[q], 0) != cudaSuccess) st = POD_ECUDA;
+        if (st == POD_OK &&
+            cudaMemcpy2DAsync(buf[q], ldb * es, (const char *)A_host + (size_t)j0 * p->lda * es, p->lda * es, m * es,
+                              w, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            st = POD_ECUDA;
+        if (st == POD_OK && cudaEventRecord(ev_copied[q], cs) != cudaSuccess) st = POD_ECUDA;
+        if (st != POD_OK) cudaGetLastError();
+    };
+    copy_block(0);
+    int racc = 0, cur = 0;
+    for (int b = 0; b < blocks && st == POD_OK; ++b) {
+        const int q = b & 1;
+        const int64_t w = (b + 1) * n / blocks - b * n / blocks;
+        if (cudaStreamWaitEvent(s, ev_copied[q], 0) != cudaSuccess) {
+            cudaGetLastError();
+            st = POD_ECUDA;
+            break;
+        }
+        if (b + 1 < blocks) copy_block(b + 1);   // streams while this block is processed
+        // ISMA on the block: same parameters, r modes kept, no refinement
+        const int wi = (cache_w[q][0] == w || cache_w[q][0] == 0) ? 0 : 1;
+        pod_ctx *cb = cache[q][wi];
+        if (!cb) {
+            pod_params pb = *p;
+            pb.n = w;
+            pb.lda = ldb;
+            pb.k = r;
+            pb.refine = 0;
+            st = pod_init(&cb, &pb, buf[q], stream);
+            if (st != POD_OK) break;
+            cache[q][wi] = cb;
+            cache_w[q][wi] = w;
+        } else {
+            st = pod_reset(cb, buf[q]);
+            if (st != POD_OK) break;
+        }
+        int32_t done = 0, steps = 0;
+        while (st == POD_OK && !done) {
+            st = pod_iterate(cb, 1 << 20, &done, nullptr, &steps);
+            if (steps == 0) break;
+        }
+        if (st != POD_OK) break;
+        if (cudaEventRecord(ev_free[q], s) != cudaSuccess) {
+            cudaGetLastError();
+            st = POD_ECUDA;
+            break;
+        }
+        const int rb = cb->hstate->r_cur;
+        if (rb == 0) continue;
+        int grid = (int)((m * rb + 255) / 256);
+        if (grid > 4 * sms) grid = 4 * sms;
+        if (p->dtype == POD_F32)
+            k_scale_cols<float><<<grid, 256, 0, s>>>((const float *)cb->U, m, rb, cb->sigma, (float *)Cb);
+        else
+            k_scale_cols<double><<<grid, 256, 0, s>>>((const double *)cb->U, m, rb, cb->sigma, (double *)Cb);
+        if (cudaGetLastError() != cudaSuccess) {
+            st = POD_ECUDA;
+            break;
+        }
+        // BLOCK MERGE of the running factors with the block's (Algorithm 3)
+        int32_t rn = 0;
+        st = pod_block_merge(p->dtype, m, racc > 0 ? Ua[cur] : nullptr, racc > 0 ? sa[cur] : nullptr, racc, Cb, m,
+                             rb, r, p->core, Ua[cur ^ 1], sa[cur ^ 1], &rn, stream);
+        if (st != POD_OK) break;
+        racc = rn;
+        cur ^= 1;
+    }
+    if (st == POD_OK) {
+        // the first k modes with the sign convention of pod_modes
+        const int k = p->k;
+        if (racc > 0) {
+            if (p->dtype == POD_F32)
+                st = launch_sign_dots<float>((const float *)Ua[cur], m, m, racc, p->seed, part, sgrid, s);
+            else
+                st = launch_sign_dots<double>((const double *)Ua[cur], m, m, racc, p->seed, part, sgrid, s);
+            if (st == POD_OK) st = launch_reduce(part, sgrid, racc, racc, dots, nullptr, s);
+        }
+        int grid = (int)((m * k + 255) / 256);
+        if (grid > 4 * sms) grid = 4 * sms;
+        if (st == POD_OK) {
+            if (p->dtype == POD_F32)
+                k_write_modes<float><<<grid, 256, 0, s>>>((const float *)Ua[cur], m, racc, k, sa[cur], dots,
+                                                          (float *)U_dev, sigma_dev);
+            else
+                k_write_modes<double><<<grid, 256, 0, s>>>((const double *)Ua[cur], m, racc, k, sa[cur], dots,
+                                                           (double *)U_dev, sigma_dev);
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = POD_ECUDA;
+        }
+    }
+    if (st != POD_OK) cudaGetLastError();
+    if (s) cudaStreamSynchronize(s);
+    if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
+        if (ev_free[i]) cudaEventDestroy(ev_free[i]);
+        for (int j = 0; j < 2; ++j)
+            if (cache[i][j]) pod_destroy(cache[i][j]);
+    }
+    void *bufs[] = {buf[0], buf[1], Cb, Ua[0], Ua[1], sa[0], sa[1], dots, part};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
     return st;
 }
 

@@ -30,7 +30,7 @@ POD_PREC_F32, POD_PREC_BF16, POD_PREC_BF16X3, POD_PREC_TF32X3 = 0, 1, 2, 3
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
             "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
-            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu"]
+            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental"]
 
 ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "core_svd", "update", "finish"]
 ORT_KERNELS = ["ort_atu", "ort_values"]
@@ -332,6 +332,42 @@ def colnorms(A, stream=None):
     _check(lib().pod_colnorms(_ptr(A), _dtype_code(A), A.shape[0], A.shape[1], A.stride(1), _ptr(s),
                               _stream(stream)), "pod_colnorms")
     return s
+
+
+def incremental(A_host, k: int, c: int, blocks: int, r: int = 0, col_strategy: str = "unf",
+                criterion: str = "subspace", tol: float = 1e-8, max_iter: int = 0, seed: int = 0x5107,
+                core: str = "auto", rows: bool = False, row_strategy: str = "l2n", w: int = 0,
+                precision: str = "f32", device=None, stream=None):
+    """Algorithm 3 on a host matrix (pod_incremental): column blocks streamed
+    to the device, ISMA per block, BLOCK MERGE.  A_host: CPU tensor (m, n),
+    column-major (pinned for overlap).  Returns (U (m, k), sigma (k,)) on the
+    device."""
+    import torch
+    if A_host.is_cuda or A_host.dim() != 2 or A_host.stride(0) != 1 or A_host.stride(1) < A_host.shape[0]:
+        raise ValueError("A_host must be a (m, n) column-major CPU tensor")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    m, n = int(A_host.shape[0]), int(A_host.shape[1])
+    p = PodParams()
+    p.m, p.n, p.lda = m, n, int(A_host.stride(1))
+    p.k, p.c, p.w, p.r = int(k), int(c), int(w), int(r)
+    p.rows = 1 if rows else 0
+    p.col_strategy = _STRATEGY[col_strategy]
+    p.row_strategy = _ROW_STRATEGY[row_strategy]
+    p.criterion = _CRITERION[criterion]
+    p.tol = float(tol)
+    p.max_iter = int(max_iter)
+    p.refine = 0
+    p.dtype = _dtype_code(A_host)
+    p.core = _CORE[core]
+    p.seed = int(seed) & ((1 << 64) - 1)
+    p.precision = _PRECISION[precision]
+    U = torch.empty((int(k), m), dtype=A_host.dtype, device=dev).t()
+    sig = torch.empty(int(k), dtype=torch.float64, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        _check(lib().pod_incremental(ctypes.byref(p), ctypes.c_void_p(A_host.data_ptr()), int(blocks), _ptr(U),
+                                     _ptr(sig), _stream(st)), "pod_incremental")
+    return U, sig
 
 
 def atu(A, U, precision: str = "f32", stream=None):
