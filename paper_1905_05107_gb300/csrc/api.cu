@@ -130,6 +130,10 @@ struct pod_ctx {
     unsigned *r_cnt, *counters_w;
     int32_t *r_rows, *r_rcnt, *r_h;
     void *Cbuf;
+    // wide sizes: global scratch for the tall passes, the core, the first
+    // CholeskyQR kernel and the refinement when their shared memory would not fit
+    unsigned char *tall_gs, *core_gs, *chol_gs, *refine_gs, *ytall_gs;
+    int jac_smem;
     // pod_backward tape (keep_tape = 1): host copy of the device TapePtrs
     TapePtrs tape_h;
     TapePtrs *tape_d;
@@ -170,7 +174,7 @@ static void ctx_free(pod_ctx *c) {
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
                     c->r_rcnt, c->r_h, c->Cbuf, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
-                    c->tc_part, c->tc_counters};
+                    c->tc_part, c->tc_counters, c->tall_gs, c->core_gs, c->chol_gs, c->refine_gs, c->ytall_gs};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->tape_h.U) cudaFree(c->tape_h.U);
@@ -202,6 +206,7 @@ static pod_status check_params(const pod_params *p) {
     if (p->keep_tape && (p->rows || p->block_trunc)) return POD_EUNSUPPORTED;
     if (p->reserved != 0) return POD_EINVAL;
     if (p->c > 256 || (p->r > 0 ? p->r : p->k) > 256) return POD_EUNSUPPORTED;
+    if (p->c + (p->r > 0 ? p->r : p->k) > 320) return POD_EUNSUPPORTED;   // Jacobi holds n_c <= 320
     if (!(p->tol == p->tol)) return POD_EINVAL;
     return POD_OK;
 }
@@ -238,6 +243,8 @@ static TallArgs<T> tall_args(pod_ctx *c, double *part, int64_t stride) {
     a.M1 = c->M1;
     a.Xm = c->Xm;
     a.Ym = c->Ym;
+    a.gscratch = c->plan.wide ? c->tall_gs : nullptr;
+    a.gstride = c->plan.gstride;
     return a;
 }
 
@@ -266,6 +273,9 @@ static SmallArgs small_args(pod_ctx *c) {
     s.Xm = c->Xm;
     s.Ym = c->Ym;
     s.hist_measure = c->hist_measure;
+    s.gws_core = c->core_gs;
+    s.jac_smem = c->jac_smem;
+    s.gws_chol = c->chol_gs;
     return s;
 }
 
@@ -558,6 +568,9 @@ static pod_status run_refine(pod_ctx *c) {
     ya.gsum = c->gsum;
     ya.counters = c->counters;
     ya.vec = (n % 2) == 0;
+    ya.gscratch = yplan.wide ? c->ytall_gs : nullptr;
+    ya.gstride = yplan.gstride;
+    if (yplan.wide && !c->ytall_gs) return POD_EUNSUPPORTED;
     const size_t part_cap = (size_t)c->plan.grid * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax);
     const size_t gsum_cap = (size_t)(c->plan.groups + 1) * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax);
     if ((size_t)yplan.grid * r * r > part_cap || (size_t)(yplan.groups + 1) * r * r > gsum_cap ||
@@ -579,6 +592,7 @@ static pod_status run_refine(pod_ctx *c) {
     ra.sigma = c->rsig;
     ra.VR = c->rVR;
     ra.K = c->rK;
+    ra.gws = c->refine_gs;
     POD_TRY(launch_refine_chol(ra, s));
     c->launches += 1;
     k_set_state<<<1, 32, 0, s>>>(c->aux + 2, 0, r, 0, 1, 1);
@@ -601,6 +615,8 @@ static pod_status run_refine(pod_ctx *c) {
     ua.Ym = c->Ym;
     TallPlan uplan = tall_plan(c->p.dtype, m, r, c->cmax, c->sms);
     ua.bm = uplan.bm;
+    ua.gscratch = uplan.wide ? c->tall_gs : nullptr;   // (r, cmax) needs no more than the round's plan
+    ua.gstride = uplan.gstride;
     POD_TRY(launch_tall<T>(TALL_UPDATE, ua, uplan, s));
     c->launches += 1;
     POD_CUDA_TRY(cudaMemcpyAsync(c->sigma, c->rsig, r * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -878,8 +894,15 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         free(c);
         return POD_EUNSUPPORTED;
     }
-    if (core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) > 220 * 1024 ||
-        small_chol_smem(c->cmax) > 220 * 1024 || c->plan.smem > 227 * 1024) {
+    const bool wide_core = core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) > 220 * 1024;
+    const bool wide_chol = small_chol_smem(c->cmax) > 220 * 1024;
+    const bool wide_refine = refine_gws_bytes(c->rmax) > 220 * 1024;
+    c->jac_smem = wide_core && core_jacobi_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) <= 200 * 1024;
+    if (wide_core && (p->rows || p->block_trunc)) {
+        free(c);
+        return POD_EUNSUPPORTED;
+    }
+    if (c->plan.smem > 227 * 1024) {
         free(c);
         return POD_EUNSUPPORTED;
     }
@@ -946,6 +969,14 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         ALLOC(c->r_h, 1);
     }
     if (p->keep_tape) ALLOC(c->tape_d, 1);
+    if (c->plan.wide) ALLOC(c->tall_gs, (size_t)c->plan.grid * c->plan.gstride);
+    if (wide_core) ALLOC(c->core_gs, core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32));
+    if (wide_chol) ALLOC(c->chol_gs, small_chol_smem(c->cmax));
+    if (wide_refine) ALLOC(c->refine_gs, refine_gws_bytes(c->rmax));
+    {
+        const TallPlan yp = tall_plan(POD_F64, n, rm, rm, c->sms);
+        if (yp.wide) ALLOC(c->ytall_gs, (size_t)yp.grid * yp.gstride);
+    }
     if (c->use_tc) {
         ALLOC(c->tc_part, c->tcplan.part_doubles);
         ALLOC(c->tc_counters, c->tcplan.mtiles);

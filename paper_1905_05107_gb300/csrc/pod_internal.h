@@ -64,6 +64,8 @@ struct TallArgs {
     const double *M1;       // g x g, ld cmax (upper triangular)
     const double *Xm;       // r x rn, ld rmax
     const double *Ym;       // g x rn, ld rmax
+    unsigned char *gscratch;   // wide plans: per-CTA slices of gstride bytes (else null)
+    int64_t gstride;
 };
 
 enum TallKind { TALL_PROJ = 0, TALL_CGS = 1, TALL_QR2 = 2, TALL_UPDATE = 3 };
@@ -73,6 +75,8 @@ struct TallPlan {
     int bm;
     int groups;
     size_t smem;
+    int wide;               // coefficient tiles and FP64 accumulators in global scratch
+    int64_t gstride;        // bytes of scratch per CTA (wide plans)
 };
 
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms);
@@ -309,6 +313,9 @@ struct SmallArgs {
     double *R1p;            // g x g, ld cmax
     double *E;              // nc x nc scratch (column-major, ld rmax + cmax)
     const struct TapePtrs *tape;   // per-round merge record for pod_backward (or null)
+    unsigned char *gws_core;       // wide cores: global scratch (core_gws_bytes), else null
+    int jac_smem;                  // wide cores: 1 = Jacobi arrays still in shared memory
+    unsigned char *gws_chol;       // wide first-CholeskyQR kernel: global scratch, else null
     double *Xm;             // r x rn, ld rmax
     double *Ym;             // g x rn, ld rmax
     double *hist_measure;   // per-round measure
@@ -316,6 +323,7 @@ struct SmallArgs {
 pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s);
 pod_status launch_core(const SmallArgs &a, cudaStream_t s);
 size_t core_smem_bytes(int rmax, int cmax, int dtype);
+size_t core_jacobi_bytes(int rmax, int cmax, int dtype);   // shared memory of the Jacobi arrays alone
 size_t small_chol_smem(int cmax);
 pod_status launch_finish(DevState *st, cudaStream_t s);
 
@@ -329,8 +337,10 @@ struct RefineArgs {
     double *sigma;          // out: r
     double *VR;             // out: r x r (ld r), U <- U VR
     double *K;              // out: r x r (ld r), V <- Y K
+    unsigned char *gws;     // wide refinements: global scratch (refine_gws_bytes), else null
 };
 pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s);
+size_t refine_gws_bytes(int r);   // bytes of the refinement kernels' work arrays
 
 // ICRS: from G_W = W^T W (g x g, ld cmax) the inputs of a core SVD whose
 // left singular vectors are the eigenvectors of G_W (R1p = R_hat with

@@ -268,12 +268,15 @@ __device__ int jacobi_lp(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *al
     return sweep;
 }
 
-// Half-warp pairs: 4 elements per lane up to 64 columns, 10 above.
+// Half-warp pairs: 4 elements per lane up to 64 columns, 10 up to 160, 20 up
+// to 320.
 template <typename J>
 __device__ int jacobi_hw(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *alpha, J tol, int max_sweeps,
                          int *s_flag) {
     if (nrow <= 64 && ncol <= 64) return jacobi_lp<J, 16, 4>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
-    return jacobi_lp<J, 16, 10>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
+    if (nrow <= 160 && ncol <= 160)
+        return jacobi_lp<J, 16, 10>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
+    return jacobi_lp<J, 16, 20>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
 }
 
 // rank of each of n keys in descending order (ties by index) -> order[rank] = i
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     const int r = st->r_cur, g = st->g, nc = r + g;
     const int ld = a.cmax;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Carve cv{smem_raw};
+    Carve cv{a.gws_chol ? a.gws_chol : smem_raw};
     X *W = cv.take<X>((size_t)ld * ld);
     X *R = cv.take<X>((size_t)ld * ld);
     X *Mw = cv.take<X>((size_t)ld * ld);
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
 size_t small_chol_smem(int cmax) { return 4 * al16x((size_t)cmax * cmax * 8) + al16x((size_t)cmax * 8) + 64; }
 
 pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s) {
-    const size_t smem = small_chol_smem(a.cmax);
+    const size_t smem = a.gws_chol ? 64 : small_chol_smem(a.cmax);
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     if (a.dtype == POD_F32) {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -506,6 +509,10 @@ size_t core_smem_bytes(int rmax, int cmax, int dtype) {
     return core_layout(rmax, cmax, dtype == POD_F32 ? 4 : 8).total;
 }
 
+size_t core_jacobi_bytes(int rmax, int cmax, int dtype) {
+    return core_layout(rmax, cmax, dtype == POD_F32 ? 4 : 8).phaseB + 64;
+}
+
 template <typename X, typename J>
 __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     DevState *st = a.st;
@@ -526,11 +533,13 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     clk[0] = clock64();
     if (tid == 0) s_bad = 0;
     const CoreLayout CL = core_layout(a.rmax, a.cmax, (int)sizeof(J));
-    Carve keep{smem_raw};
+    // wide cores: everything but the Jacobi arrays in global scratch
+    unsigned char *gbase = a.gws_core;
+    Carve keep{gbase ? gbase : smem_raw};
     X *Ex = keep.take<X>((size_t)nmax * nmax);    // E, column-major, ld nc
     X *Rinv = keep.take<X>((size_t)ld * ld);      // g x g, ld cmax
     X *Ptx = keep.take<X>((size_t)a.rmax * ld);   // r x g, ld cmax
-    unsigned char *work = smem_raw + CL.keep;
+    unsigned char *work = (gbase ? gbase : smem_raw) + CL.keep;
 
     // ---- phase A: R2 = chol(G2), M2 = R2^{-1}, R = R2 R1p, Rinv = M1 M2, E
     if (sizeof(J) == 4) {
@@ -715,11 +724,13 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     }
 
     // ---- phase B: Jacobi on the rows of E: B = E^T (column p = row p of E)
-    Carve cv{work};
-    J *B = cv.take<J>((size_t)nmax * nmax);
-    J *V = cv.take<J>((size_t)nmax * nmax);
-    J *alpha = cv.take<J>(nmax);
-    int *order = cv.take<int>(nmax);
+    // (wide cores: B, V in shared memory when they fit, else in global scratch)
+    Carve cvB{(gbase && a.jac_smem) ? smem_raw : work};
+    J *B = cvB.take<J>((size_t)nmax * nmax);
+    J *V = cvB.take<J>((size_t)nmax * nmax);
+    J *alpha = cvB.take<J>(nmax);
+    int *order = cvB.take<int>(nmax);
+    Carve cv = (gbase && a.jac_smem) ? Carve{work} : cvB;
     X *Vr = cv.take<X>((size_t)nmax * a.rmax);
     X *Q = cv.take<X>((size_t)nmax * a.rmax);
     X *Yt = cv.take<X>((size_t)nmax * a.rmax);
@@ -939,7 +950,8 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
 
 pod_status launch_core(const SmallArgs &a, cudaStream_t s) {
     const bool f64 = a.core_f64 || a.dtype == POD_F64;
-    const size_t smem = core_smem_bytes(a.rmax, a.cmax, f64 ? POD_F64 : POD_F32);
+    size_t smem = core_smem_bytes(a.rmax, a.cmax, f64 ? POD_F64 : POD_F32);
+    if (a.gws_core) smem = a.jac_smem ? core_jacobi_bytes(a.rmax, a.cmax, f64 ? POD_F64 : POD_F32) : 64;
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     if (!f64) {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_core<dfloat, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -978,7 +990,7 @@ pod_status launch_finish(DevState *st, cudaStream_t s) {
 __global__ void __launch_bounds__(CHOL_THREADS) k_refine_chol(RefineArgs a) {
     const int r = a.r;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Carve cv{smem_raw};
+    Carve cv{a.gws ? a.gws : smem_raw};
     double *W = cv.take<double>((size_t)r * r);
     double *R = cv.take<double>((size_t)r * r);
     double *Mw = cv.take<double>((size_t)r * r);
@@ -1007,7 +1019,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_refine_chol(RefineArgs a) {
 __global__ void __launch_bounds__(CORE_THREADS) k_refine_svd(RefineArgs a) {
     const int r = a.r;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Carve cv{smem_raw};
+    Carve cv{a.gws ? a.gws : smem_raw};
     double *W = cv.take<double>((size_t)r * r);
     double *R2 = cv.take<double>((size_t)r * r);
     double *M2 = cv.take<double>((size_t)r * r);
@@ -1147,8 +1159,12 @@ pod_status launch_rows_setg(DevState *st, const DevState *stc, cudaStream_t s) {
     return POD_OK;
 }
 
+size_t refine_gws_bytes(int r) {
+    return 8 * al16x((size_t)r * r * 8) + al16x((size_t)r * 8) + al16x((size_t)r * 4) + 64;
+}
+
 pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s) {
-    const size_t smem = 4 * al16x((size_t)a.r * a.r * 8) + 64;
+    const size_t smem = a.gws ? 64 : 4 * al16x((size_t)a.r * a.r * 8) + 64;
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     POD_CUDA_TRY(cudaFuncSetAttribute(k_refine_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_refine_chol<<<1, CHOL_THREADS, smem, s>>>(a);
@@ -1157,7 +1173,7 @@ pod_status launch_refine_chol(const RefineArgs &a, cudaStream_t s) {
 }
 
 pod_status launch_refine_svd(const RefineArgs &a, cudaStream_t s) {
-    const size_t smem = 8 * al16x((size_t)a.r * a.r * 8) + al16x((size_t)a.r * 8) + al16x((size_t)a.r * 4) + 64;
+    const size_t smem = a.gws ? 64 : 8 * al16x((size_t)a.r * a.r * 8) + al16x((size_t)a.r * 8) + al16x((size_t)a.r * 4) + 64;
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
     POD_CUDA_TRY(cudaFuncSetAttribute(k_refine_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_refine_svd<<<1, CORE_THREADS, smem, s>>>(a);

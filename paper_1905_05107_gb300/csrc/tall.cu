@@ -242,6 +242,17 @@ __host__ __device__ inline size_t smem_bytes(const SmemPlan &p) {
     return (2 * p.buf + p.ws + p.s1 + p.s2 + p.s3) * sizeof(T) + (p.acc1 + p.acc2) * 8 +
            (size_t)TALL_THREADS * 16 * sizeof(T) + 64;
 }
+// Wide plans keep only the slab buffers and the reduction tile in shared
+// memory; the coefficient tiles S1..S3 and the FP64 accumulators live in the
+// CTA's slice of global scratch (L2-resident).
+template <typename T>
+__host__ __device__ inline size_t smem_bytes_wide(const SmemPlan &p) {
+    return (2 * p.buf + p.ws) * sizeof(T) + (size_t)TALL_THREADS * 16 * sizeof(T) + 64;
+}
+template <typename T>
+__host__ __device__ inline size_t gscratch_bytes(const SmemPlan &p) {
+    return (((p.s1 + p.s2 + p.s3) * sizeof(T) + 15) / 16) * 16 + (p.acc1 + p.acc2) * 8;
+}
 
 template <typename T, int KIND>
 __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
@@ -255,12 +266,24 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     T *buf0 = reinterpret_cast<T *>(smem_raw);
     T *buf1 = buf0 + L.buf;
     T *Ws = buf1 + L.buf;
-    T *S1 = Ws + L.ws;
-    T *S2 = S1 + L.s1;
-    T *S3 = S2 + L.s2;
-    double *acc1 = reinterpret_cast<double *>(S3 + L.s3);
-    double *acc2 = acc1 + L.acc1;
-    T *red = reinterpret_cast<T *>(acc2 + L.acc2);
+    T *S1, *S2, *S3, *red;
+    double *acc1, *acc2;
+    if (a.gscratch) {
+        unsigned char *gs = a.gscratch + (int64_t)blockIdx.x * a.gstride;
+        S1 = reinterpret_cast<T *>(gs);
+        S2 = S1 + L.s1;
+        S3 = S2 + L.s2;
+        acc1 = reinterpret_cast<double *>(gs + (((L.s1 + L.s2 + L.s3) * sizeof(T) + 15) / 16) * 16);
+        acc2 = acc1 + L.acc1;
+        red = Ws + L.ws;
+    } else {
+        S1 = Ws + L.ws;
+        S2 = S1 + L.s1;
+        S3 = S2 + L.s2;
+        acc1 = reinterpret_cast<double *>(S3 + L.s3);
+        acc2 = acc1 + L.acc1;
+        red = reinterpret_cast<T *>(acc2 + L.acc2);
+    }
     int *s_flag = reinterpret_cast<int *>(red + TALL_THREADS * 16);
     const int tid = threadIdx.x, bd = blockDim.x;
     const int r4 = round4(r), g4 = round4(g), rn4 = round4(rn);
@@ -555,10 +578,29 @@ TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
         per_sm = 1;
         for (int b = 128; b >= 16 && !bm; b >>= 1)
             if (bytes_for(b) <= 200 * 1024) bm = b;
-        if (!bm) bm = 16;
     }
-    p.bm = bm;
-    p.smem = bytes_for(bm);
+    if (bm) {
+        p.bm = bm;
+        p.smem = bytes_for(bm);
+    } else {
+        // wide: coefficient tiles and accumulators in global scratch
+        auto wide_for = [&](int b) {
+            SmemPlan L = smem_plan(rmax, cmax, b);
+            return f32 ? smem_bytes_wide<float>(L) : smem_bytes_wide<double>(L);
+        };
+        per_sm = 1;
+        bm = 16;
+        for (int b = 64; b >= 16; b >>= 1)
+            if (wide_for(b) <= 200 * 1024) {
+                bm = b;
+                break;
+            }
+        SmemPlan L = smem_plan(rmax, cmax, bm);
+        p.bm = bm;
+        p.smem = wide_for(bm);
+        p.wide = 1;
+        p.gstride = (int64_t)(f32 ? gscratch_bytes<float>(L) : gscratch_bytes<double>(L));
+    }
     const int64_t slabs = (m + bm - 1) / bm;
     int64_t grid = (int64_t)per_sm * num_sms;
     if (grid > slabs) grid = slabs;
