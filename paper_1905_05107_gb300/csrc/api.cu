@@ -484,6 +484,25 @@ static pod_status enqueue_round(pod_ctx *c) {
     ta.out = c->G2;
     POD_TRY(launch_tall<T>(TALL_QR2, ta, c->plan, s));
     mark(c);
+    // when G2 is far from I (flagged by the QR2 pass itself) the residual
+    // block was too ill-conditioned for an FP32 first Gram: redo CGS with a
+    // compensated Gram, the Cholesky and QR2; otherwise these return at once
+    {
+        TallArgs<T> tr = ta;
+        tr.cond = 1;
+        SmallArgs sr = sm;
+        sr.cond = 1;
+        tr.part_stride = sPG;
+        tr.out = c->PG;
+        POD_TRY(launch_tall<T>(TALL_CGS, tr, c->plan, s));
+        mark(c);
+        POD_TRY(launch_small_chol(sr, s));
+        mark(c);
+        tr.part_stride = (int64_t)c->cmax * c->cmax;
+        tr.out = c->G2;
+        POD_TRY(launch_tall<T>(TALL_QR2, tr, c->plan, s));
+        mark(c);
+    }
     POD_TRY(launch_core(sm, s));
     mark(c);
     POD_TRY(launch_tall<T>(TALL_UPDATE, ta, c->plan, s));

@@ -31,6 +31,9 @@ struct DevState {
     double sin_max;
     double cos_min;
     long long core_cycles[6];   // last core SVD: clock64 deltas of its phases
+    int robust;     // this round's second CholeskyQR Gram was far from I: redo
+                    // the first pass with a compensated Gram (set by k_check_g2)
+    int robust_rounds;   // rounds that needed it
 };
 
 // ---------------------------------------------------------------------------
@@ -237,8 +240,9 @@ constexpr int RED_GROUP = 16;
 // Sum of FP64 partials inside the kernel: the last CTA to arrive in each
 // group of RED_GROUP CTAs sums that group's partials; the last group to
 // finish sums the group results.  Orders are fixed by block index; arrival
-// counters are reset by the CTAs that consumed them.
-__device__ inline void tall_reduce(const double *part, double *gsum, double *out, int count, int64_t stride,
+// counters are reset by the CTAs that consumed them.  Returns true on the CTA
+// that wrote the final sums.
+__device__ inline bool tall_reduce(const double *part, double *gsum, double *out, int count, int64_t stride,
                             unsigned *counters, int *s_flag) {
     const int tid = threadIdx.x;
     const int grid = gridDim.x;
@@ -249,7 +253,7 @@ __device__ inline void tall_reduce(const double *part, double *gsum, double *out
     __syncthreads();
     if (tid == 0) *s_flag = (atomicAdd(&counters[grp], 1u) == (unsigned)(gsize - 1));
     __syncthreads();
-    if (!*s_flag) return;
+    if (!*s_flag) return false;
     __threadfence();
     for (int e = tid; e < count; e += blockDim.x) {
         double s = 0.0;
@@ -263,7 +267,7 @@ __device__ inline void tall_reduce(const double *part, double *gsum, double *out
         *s_flag = (atomicAdd(&counters[ngroups], 1u) == (unsigned)(ngroups - 1));
     }
     __syncthreads();
-    if (!*s_flag) return;
+    if (!*s_flag) return false;
     __threadfence();
     for (int e = tid; e < count; e += blockDim.x) {
         double s = 0.0;
@@ -271,4 +275,5 @@ __device__ inline void tall_reduce(const double *part, double *gsum, double *out
         out[e] = s;
     }
     if (tid == 0) counters[ngroups] = 0;
+    return true;   // this CTA wrote out (the last to arrive)
 }

@@ -66,6 +66,9 @@ struct TallArgs {
     const double *Ym;       // g x rn, ld rmax
     unsigned char *gscratch;   // wide plans: per-CTA slices of gstride bytes (else null)
     int64_t gstride;
+    int cond;               // 1: run only when st->robust is set (and then with a
+                            // compensated Gram in the CGS pass); the QR2 pass with
+                            // cond = 0 sets st->robust from its G2
 };
 
 enum TallKind { TALL_PROJ = 0, TALL_CGS = 1, TALL_QR2 = 2, TALL_UPDATE = 3 };
@@ -297,6 +300,7 @@ pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t
 
 struct SmallArgs {
     DevState *st;
+    int cond;               // 1: run only when st->robust is set
     int dtype;              // storage type (rounding of coefficients)
     int core_f64;           // arithmetic of the core SVD
     int64_t m;
@@ -326,6 +330,7 @@ size_t core_smem_bytes(int rmax, int cmax, int dtype);
 size_t core_jacobi_bytes(int rmax, int cmax, int dtype);   // shared memory of the Jacobi arrays alone
 size_t small_chol_smem(int cmax);
 pod_status launch_finish(DevState *st, cudaStream_t s);
+
 
 // refinement QR(A^T U), SVD(R)
 struct RefineArgs {

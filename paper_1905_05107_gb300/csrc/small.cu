@@ -398,6 +398,7 @@ template <typename X>
 __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     DevState *st = a.st;
     if (st->done) return;
+    if (a.cond && !st->robust) return;
     const int r = st->r_cur, g = st->g, nc = r + g;
     const int ld = a.cmax;
     extern __shared__ __align__(16) unsigned char smem_raw[];

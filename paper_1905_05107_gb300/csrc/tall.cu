@@ -172,6 +172,70 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
     __syncthreads();
 }
 
+// As gram_acc for a symmetric X^T X with every product split exactly
+// (TwoProduct) and summed with TwoSum: the tile sums carry ~44 bits before the
+// FP64 flush.  Used for the first CholeskyQR Gram when the plain FP32 one
+// proved too inexact (ill-conditioned residual blocks).  Ends with a barrier.
+template <typename T>
+__device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, int ldacc) {
+    const int ta = (na + 3) >> 2, nT = ta * ta, chunks = bm >> 2;
+    for (int tile = threadIdx.x; tile < nT; tile += blockDim.x) {
+        const int ti = tile / ta, tj = tile - ti * ta;
+        if (ti > tj) continue;
+        if constexpr (sizeof(T) == 4) {
+            float hi[16], lo[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
+            for (int rc = 0; rc < chunks; ++rc) {
+                float x[4][4], y[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) lds4(X + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const float p = x[u][w] * y[v][w];
+                            const float e = fmaf(x[u][w], y[v][w], -p);
+                            const dfloat s = df_two_sum(hi[u * 4 + v], p);
+                            hi[u * 4 + v] = s.hi;
+                            lo[u * 4 + v] += s.lo + e;
+                        }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    acc[(4 * ti + u) * ldacc + 4 * tj + v] += (double)hi[u * 4 + v] + (double)lo[u * 4 + v];
+        } else {
+            double a[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) a[e] = 0.0;
+            for (int rc = 0; rc < chunks; ++rc) {
+                double x[4][4], y[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) lds4(X + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) a[u * 4 + v] = fma(x[u][w], y[v][w], a[u * 4 + v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[(4 * ti + u) * ldacc + 4 * tj + v] += a[u * 4 + v];
+        }
+    }
+    __syncthreads();
+}
+
 // Row-space products on a slab, tiled 4 rows x 4 output columns:
 // a1 = A1 S1 (K1 terms), a2 = A2 S2 (K2 terms); A1, A2 column-major (ld);
 // S1, S2 row-major with leading dimensions ls1, ls2; tri: S1 is upper
@@ -258,6 +322,7 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     const DevState *st = a.st;
     if (st->done) return;
+    if (a.cond && !st->robust) return;
     const int r = st->r_cur, g = st->g, rn = st->r_new;
     const int bm = a.bm;
     const SmemPlan L = smem_plan(a.rmax, a.cmax, bm);
@@ -367,7 +432,8 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                 __syncthreads();
                 gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, L.c4, red);
             }
-            gram_acc<T>(Cs, g, Cs, g, ld, bm, true, acc2, L.c4, red);
+            if (a.cond) gram_acc_comp<T>(Cs, g, ld, bm, acc2, L.c4);
+            else gram_acc<T>(Cs, g, Cs, g, ld, bm, true, acc2, L.c4, red);
         } else if (KIND == TALL_QR2) {
             if (r > 0) {
                 rowspace_tiles<T>(bm, g, Us, r, S1, g4, Us, r, S2, g4, ld, false,
@@ -445,7 +511,36 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
             if (p <= q) out[p * a.cmax + q] = acc2[p * L.c4 + q];
         }
     }
-    tall_reduce(a.part, a.gsum, a.out, (int)a.part_stride, a.part_stride, a.counters, s_flag);
+    const bool last = tall_reduce(a.part, a.gsum, a.out, (int)a.part_stride, a.part_stride, a.counters, s_flag);
+    if (KIND == TALL_QR2 && !a.cond && last) {
+        // the second CholeskyQR Gram must be near I on its kept indices; if
+        // not, the first pass lost accuracy (an ill-conditioned residual
+        // block): flag the round for the compensated rerun
+        __threadfence();
+        double dev = 0.0;
+        for (int e = tid; e < g * g; e += bd) {
+            const int i = e / g, j = e - i * g;
+            if (i > j) continue;
+            const double gii = __ldcg(a.out + i * a.cmax + i), gjj = __ldcg(a.out + j * a.cmax + j);
+            if (gii == 0.0 || gjj == 0.0) continue;   // dropped index
+            const double d = fabs(__ldcg(a.out + i * a.cmax + j) - (i == j ? 1.0 : 0.0));
+            dev = (d != d) ? 1e300 : (d > dev ? d : dev);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, dev, o);
+            dev = y > dev ? y : dev;
+        }
+        __shared__ double wmax[TALL_THREADS / 32];
+        if ((tid & 31) == 0) wmax[tid >> 5] = dev;
+        __syncthreads();
+        if (tid == 0) {
+            double mx = 0.0;
+            for (int w = 0; w < TALL_THREADS / 32; ++w) mx = wmax[w] > mx ? wmax[w] : mx;
+            DevState *sw = const_cast<DevState *>(st);
+            sw->robust = mx > 0.1;
+            if (mx > 0.1) sw->robust_rounds += 1;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -48,3 +48,16 @@ def test_incremental_flow_f32():
     U, s = pod.incremental(host(A), 20, 40, 3, tol=1e-8)
     np.testing.assert_allclose(s.cpu().numpy(), ref.sigma, rtol=1e-5)
     assert O.sin_principal_max(ref.U, U.double().cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-9), (np.float32, 5e-5)])
+def test_incremental_wide_cores(dtype, tol):
+    """k = 100, c = 200 (n_c = 300: wide tall passes, core SVD with its
+    Jacobi arrays in global memory) on 4 column blocks.  FP32 bar: the cut
+    at 100 of sigma_i = 0.97^i has a gap of 0.97^99 * 0.03 = 1.5e-3 of
+    sigma_1, so FP32 determines the subspace to u sigma_1 / gap = 4e-5."""
+    A = synth.planted(12000, 2400, 0.97 ** np.arange(400), 1e-6, 63, dtype)
+    ref = O.incremental_pod(A.astype(np.float64), 4, O.Params(k=100, c=200, seed=0x5107, tol=1e-8))
+    U, s = pod.incremental(host(A), 100, 200, 4, tol=1e-8)
+    np.testing.assert_allclose(s.cpu().numpy(), ref.sigma, rtol=tol)
+    assert O.sin_principal_max(ref.U, U.double().cpu().numpy()) <= tol
