@@ -186,6 +186,14 @@ POD_API pod_status pod_get_trace(pod_ctx *ctx, int32_t t, int32_t *idx_host,
 POD_API pod_status pod_wedin(pod_ctx *ctx, double *out4);
 
 /*
+ * pod_robust_rounds -- how many rounds so far needed the guarded rerun of the
+ * first CholeskyQR pass with a compensated Gram (their residual block was too
+ * ill-conditioned for an FP32 Gram: the second pass's Gram was not within 0.1
+ * of I).  Synchronises.
+ */
+POD_API pod_status pod_robust_rounds(pod_ctx *ctx, int32_t *robust_rounds);
+
+/*
  * pod_last_rows -- the row sample of the most recent ICRS iteration (SAMPLE
  * AND SCALE UNIQUE ROWS of Algorithm 1): the h distinct rows I_r in
  * ascending order and their draw counts t_hat (sum = w).  Synchronises.

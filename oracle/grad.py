@@ -58,4 +58,4 @@ def gradient(A_np: np.ndarray, index_sets, k: int, r: int, w, g, ws=None, refine
     wst = None if ws is None else torch.as_tensor(np.asarray(ws, dtype=np.float64))
     L = loss(U, s, wt, gt, wst)
     L.backward()
-    return A.grad.numpy(), float(L)
+    return A.grad.numpy(), float(L.detach())

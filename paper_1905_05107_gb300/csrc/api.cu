@@ -130,6 +130,7 @@ struct pod_ctx {
     unsigned *r_cnt, *counters_w;
     int32_t *r_rows, *r_rcnt, *r_h;
     void *Cbuf;
+    void *Wbuf;      // W = Z M1 of the current round (m x cmax, ld m), from the QR2 pass
     // wide sizes: global scratch for the tall passes, the core, the first
     // CholeskyQR kernel and the refinement when their shared memory would not fit
     unsigned char *tall_gs, *core_gs, *chol_gs, *refine_gs, *ytall_gs;
@@ -173,7 +174,7 @@ static void ctx_free(pod_ctx *c) {
                     c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
-                    c->r_rcnt, c->r_h, c->Cbuf, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
+                    c->r_rcnt, c->r_h, c->Cbuf, c->Wbuf, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
                     c->tc_part, c->tc_counters, c->tall_gs, c->core_gs, c->chol_gs, c->refine_gs, c->ytall_gs};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -469,6 +470,8 @@ static pod_status enqueue_round(pod_ctx *c) {
         ta.lda = c->p.m;
         ta.vec = (c->p.m * (int64_t)sizeof(T)) % 16 == 0;
     }
+    ta.Wout = (T *)c->Wbuf;
+    ta.ldw = c->p.m;
     ta.out = c->P;
     POD_TRY(launch_tall<T>(TALL_PROJ, ta, c->plan, s));
     mark(c);
@@ -478,6 +481,7 @@ static pod_status enqueue_round(pod_ctx *c) {
     mark(c);
     SmallArgs sm = small_args(c);
     sm.tape = c->p.keep_tape ? c->tape_d : nullptr;
+    sm.wq = 1;
     POD_TRY(launch_small_chol(sm, s));
     mark(c);
     ta.part_stride = (int64_t)c->cmax * c->cmax;
@@ -505,8 +509,17 @@ static pod_status enqueue_round(pod_ctx *c) {
     }
     POD_TRY(launch_core(sm, s));
     mark(c);
-    POD_TRY(launch_tall<T>(TALL_UPDATE, ta, c->plan, s));
-    mark(c);
+    {
+        // U <- U X + W Y with the W the QR2 pass stored (the one whose Gram gave R2)
+        TallArgs<T> ua = ta;
+        ua.A = (const T *)c->Wbuf;
+        ua.idx = nullptr;
+        ua.lda = c->p.m;
+        ua.Wout = nullptr;
+        ua.vec = (c->p.m * (int64_t)sizeof(T)) % 16 == 0;
+        POD_TRY(launch_tall<T>(TALL_UPDATE, ua, c->plan, s));
+        mark(c);
+    }
     POD_TRY(launch_finish(c->st, s));
     mark(c);
     return POD_OK;
@@ -933,6 +946,9 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     unsigned char *Ub = nullptr;
     ALLOC(Ub, (size_t)m * rm * es);
     c->U = Ub;
+    unsigned char *Wb = nullptr;
+    ALLOC(Wb, (size_t)m * cm * es);
+    c->Wbuf = Wb;
     ALLOC(c->sigma, rm);
     ALLOC(c->s, n);
     ALLOC(c->ort, n);
@@ -1394,6 +1410,14 @@ pod_status pod_core_stats(pod_ctx *c, int32_t *sweeps, int64_t *cycles) {
     if (sweeps) *sweeps = c->hstate->sweeps;
     if (cycles)
         for (int i = 0; i < 6; ++i) cycles[i] = c->hstate->core_cycles[i];
+    return POD_OK;
+}
+
+pod_status pod_robust_rounds(pod_ctx *c, int32_t *robust_rounds) {
+    if (!c || !robust_rounds) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    POD_TRY(read_state(c));
+    *robust_rounds = c->hstate->robust_rounds;
     return POD_OK;
 }
 

@@ -31,8 +31,9 @@ struct DevState {
     double sin_max;
     double cos_min;
     long long core_cycles[6];   // last core SVD: clock64 deltas of its phases
-    int robust;     // this round's second CholeskyQR Gram was far from I: redo
-                    // the first pass with a compensated Gram (set by k_check_g2)
+    int robust;     // redo this round's first CholeskyQR pass with a compensated
+                    // Gram: set by the plain Cholesky when it dropped a column its
+                    // Gram could not resolve, or by the QR2 pass when G2 is far from I
     int robust_rounds;   // rounds that needed it
 };
 

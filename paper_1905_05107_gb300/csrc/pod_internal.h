@@ -69,6 +69,8 @@ struct TallArgs {
     int cond;               // 1: run only when st->robust is set (and then with a
                             // compensated Gram in the CGS pass); the QR2 pass with
                             // cond = 0 sets st->robust from its G2
+    T *Wout;                // QR2 pass: W = (Z - U P2) M1 stored here (m x g, ld ldw),
+    int64_t ldw;            // the block the UPDATE pass then combines (or null)
 };
 
 enum TallKind { TALL_PROJ = 0, TALL_CGS = 1, TALL_QR2 = 2, TALL_UPDATE = 3 };
@@ -322,6 +324,10 @@ struct SmallArgs {
     unsigned char *gws_chol;       // wide first-CholeskyQR kernel: global scratch, else null
     double *Xm;             // r x rn, ld rmax
     double *Ym;             // g x rn, ld rmax
+    int wq;                 // 1: the UPDATE combines U and the stored W = Z M1, so
+                            // Xm = U_E[:r, :rn], Ym = R2^{-1} U_E[r:, :rn];
+                            // 0: it combines U and C, Xm = U_E[:r] - Ptot Ym,
+                            // Ym = R^{-1} U_E[r:]
     double *hist_measure;   // per-round measure
 };
 pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s);

@@ -5,7 +5,8 @@
 //   * the core E = [[Sigma_1, U_1^T C], [0, R]] (Eq. 8) and its SVD (Eq. 9);
 //   * truncation to r and to the non-zero singular values, the convergence
 //     measures of Algorithm 1, and the update coefficients X, Y with
-//     U_new = U X + C Y.
+//     U_new = U X + W Y (W = Z M1 stored by the QR2 pass), or U X + C Y
+//     for the row-block stage of ICRS.
 // The FP64 storage path computes in FP64.  The FP32 path computes the
 // triangular factors in double-float (X = dfloat), runs the one-sided Jacobi
 // sweeps of the core in FP32, and finishes with a double-float Rayleigh step
@@ -31,13 +32,14 @@ __device__ __forceinline__ double round_to(int dtype, double v) {
 // Upper Cholesky with pivot dropping, one barrier per pivot.  W (n x n, ld)
 // holds a symmetric Gram matrix in its upper triangle and is overwritten;
 // R (ld) receives the factor with R^T R = G on the kept indices.  A pivot
-// d <= thr marks its index as numerically dependent: R's row is zero
+// d <= thr (or d <= thrv[k], per index, when thrv is given) marks its index
+// as numerically dependent: R's row is zero
 // (Algorithm 2 drops the matching zero singular values of E).  The row of
 // pivot k is written to R while the trailing update reads the unscaled row
 // from W, so both happen in the same phase.
 // ---------------------------------------------------------------------------
 template <typename X>
-__device__ void chol_drop(X *W, int ldw, int n, X thr, X *R, int ldr, X *piv3) {
+__device__ void chol_drop(X *W, int ldw, int n, X thr, X *R, int ldr, X *piv3, const X *thrv = nullptr) {
     const int tid = threadIdx.x, bd = blockDim.x;
     for (int e = tid; e < n * n; e += bd) {
         const int i = e / n, j = e % n;
@@ -45,8 +47,8 @@ __device__ void chol_drop(X *W, int ldw, int n, X thr, X *R, int ldr, X *piv3) {
     }
     // piv3 = {sqrt(d), 1/sqrt(d), 1/d} of the current pivot (zeros if dropped),
     // written by the thread that produces the pivot's final value
-    auto set_pivot = [&](X d) {
-        if (x_gt(d, thr)) {
+    auto set_pivot = [&](X d, int k) {
+        if (x_gt(d, thrv ? thrv[k] : thr)) {
             const X p = XOps<X>::sqrt_(d);
             piv3[0] = p;
             piv3[1] = XOps<X>::one() / p;
@@ -55,7 +57,7 @@ __device__ void chol_drop(X *W, int ldw, int n, X thr, X *R, int ldr, X *piv3) {
             piv3[0] = piv3[1] = piv3[2] = XOps<X>::zero();
         }
     };
-    if (tid == 0 && n > 0) set_pivot(W[0]);
+    if (tid == 0 && n > 0) set_pivot(W[0], 0);
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         const X piv = piv3[0], inv_piv = piv3[1], inv_d = piv3[2];
@@ -83,7 +85,7 @@ __device__ void chol_drop(X *W, int ldw, int n, X thr, X *R, int ldr, X *piv3) {
         __syncthreads();
         if (k + 1 < n) {
             // the next pivot: updated above, or unchanged when this pivot was dropped
-            if (keep ? owner : tid == 0) set_pivot(keep ? next_d : W[(k + 1) * ldw + k + 1]);
+            if (keep ? owner : tid == 0) set_pivot(keep ? next_d : W[(k + 1) * ldw + k + 1], k + 1);
             __syncthreads();
         }
     }
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     __shared__ double red[32];
     __shared__ X piv3[3];
     X *dinv = cv.take<X>(ld);
+    X *thrv = cv.take<X>(ld);
     const int tid = threadIdx.x, bd = blockDim.x;
     const double *P2 = a.PG;
     const double *G = a.PG + (int64_t)a.rmax * a.cmax;
@@ -427,15 +430,40 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     cmax2 = block_max<double>(cmax2, red);
     const double s0 = r > 0 ? a.sigma[0] : 0.0;
     const double scale = cmax2 > s0 * s0 ? cmax2 : s0 * s0;
-    const double eps = nc * unit_roundoff(a.dtype);
-    const X thr = XOps<X>::from(eps * eps * scale);
-
+    // Pivot floors.  FP32 storage: a direction whose pivot d_j is dropped
+    // hides at most sqrt(d_j) of the block, so the floor is (8u)^2 scale
+    // (8 u sigma_1), which the compensated Gram of the rerun resolves.  The
+    // plain FP32 Gram is off by up to ~ 8 u G_jj in the pivot of column j,
+    // so there the floor for column j is also at least 8 u G_jj (smaller
+    // pivots are rounding noise).  FP64 storage: (n_c u)^2 scale.
+    const double u = unit_roundoff(a.dtype);
+    const bool f32 = a.dtype == POD_F32;
+    const double eps = f32 ? 8.0 * u : nc * u;
+    const double floor_abs = eps * eps * scale;
+    const X thr = XOps<X>::from(floor_abs);
+    const bool plain32 = f32 && !a.cond;
+    for (int j = tid; j < g; j += bd) {
+        const double tj = 8.0 * u * G[j * ld + j];
+        thrv[j] = XOps<X>::from(plain32 && tj > floor_abs ? tj : floor_abs);
+    }
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
         W[i * ld + j] = XOps<X>::from(i <= j ? G[i * ld + j] : 0.0);
     }
     __syncthreads();
-    chol_drop<X>(W, ld, g, thr, R, ld, piv3);
+    chol_drop<X>(W, ld, g, thr, R, ld, piv3, thrv);
+    if (!a.cond) {
+        // a column the plain FP32 pass dropped under its noise floor
+        // 8 u G_jj may hide more than 8 u sigma_1: the round then takes the
+        // compensated rerun.  The QR2 pass adds its own test on G2 and counts
+        // the round.
+        int flag = 0;
+        if (plain32)
+            for (int j = tid; j < g; j += bd)
+                if (x_hi(R[j * ld + j]) == 0.f && 8.0 * u * G[j * ld + j] > floor_abs) flag = 1;
+        flag = __syncthreads_or(flag);
+        if (tid == 0) st->robust = flag;
+    }
     tri_inv<X>(R, ld, g, Mw, ld, M, ld, dinv);
     // round M1 to the storage type: that is the matrix the QR2 pass applies
     for (int e = tid; e < g * g; e += bd) {
@@ -452,7 +480,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     }
 }
 
-size_t small_chol_smem(int cmax) { return 4 * al16x((size_t)cmax * cmax * 8) + al16x((size_t)cmax * 8) + 64; }
+size_t small_chol_smem(int cmax) { return 4 * al16x((size_t)cmax * cmax * 8) + 2 * al16x((size_t)cmax * 8) + 64; }
 
 pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s) {
     const size_t smem = a.gws_chol ? 64 : small_chol_smem(a.cmax);
@@ -664,9 +692,10 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
             Rif[i * ld + j] = w;
         }
         __syncthreads();
+        // Rinv keeps R2^{-1} alone when the update applies it to the stored W
         for (int e = tid; e < g * g; e += bd) {
             const int i = e / g, j = e % g;
-            Rinv[i * ld + j] = XOps<X>::from_f(Rif[i * ld + j]);
+            Rinv[i * ld + j] = XOps<X>::from_f(a.wq ? M2f[i * ld + j] : Rif[i * ld + j]);
         }
         for (int e = tid; e < nc * nc; e += bd) {
             const int q = e / nc, p = e % nc;   // column q, row p
@@ -708,7 +737,11 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         chol_drop<X>(W, ld, g, thr, R2, ld, piv3);
         tri_inv<X>(R2, ld, g, W, ld, M2, ld, dinv);
         trmm_upper<X>(R2, ld, R1, ld, g, Rr, ld);     // R = R2 R1p
-        trmm_upper<X>(M1, ld, M2, ld, g, Rinv, ld);   // Rinv = M1 M2
+        if (a.wq) {
+            for (int e = tid; e < g * g; e += bd) Rinv[(e / g) * ld + e % g] = M2[(e / g) * ld + e % g];
+        } else {
+            trmm_upper<X>(M1, ld, M2, ld, g, Rinv, ld);   // Rinv = M1 M2
+        }
         for (int e = tid; e < nc * nc; e += bd) {
             const int q = e / nc, p = e % nc;   // column q, row p
             X v = XOps<X>::zero();
@@ -902,10 +935,17 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         }
         for (int e = tid; e < g * g; e += bd) {
             const int i = e / g, j = e % g;
-            tp[TL.Rinv + i * ld + j] = XOps<X>::to(Rinv[i * ld + j]);
+            double v = 0.0;
+            if (!a.wq) {
+                v = XOps<X>::to(Rinv[i * ld + j]);
+            } else if (i <= j) {   // R^{-1} = M1 R2^{-1}
+                for (int l = i; l <= j; ++l) v = fma(a.M1[i * ld + l], XOps<X>::to(Rinv[l * ld + j]), v);
+            }
+            tp[TL.Rinv + i * ld + j] = v;
         }
     }
-    // Y = Rinv U_E[r:, :rn] (g x rn), X = U_E[:r, :rn] - Ptot Y (r x rn)
+    // wq: Y = R2^{-1} U_E[r:, :rn], X = U_E[:r, :rn]; otherwise
+    // Y = R^{-1} U_E[r:, :rn] (g x rn), X = U_E[:r, :rn] - Ptot Y (r x rn)
     for (int e = tid; e < g * rn; e += bd) {
         const int j = e / rn, q = e % rn;
         X acc = XOps<X>::zero();
@@ -920,7 +960,8 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     for (int e = tid; e < r * rn; e += bd) {
         const int l = e / rn, q = e % rn;
         X acc = Q[q * nc + l];
-        for (int j = 0; j < g; ++j) acc = acc - Ptx[l * ld + j] * Yt[j * a.rmax + q];
+        if (!a.wq)
+            for (int j = 0; j < g; ++j) acc = acc - Ptx[l * ld + j] * Yt[j * a.rmax + q];
         a.Xm[l * a.rmax + q] = XOps<X>::to(acc);
     }
     for (int s = tid; s < rn; s += bd) a.sigma[s] = XOps<X>::to(sig[s]);

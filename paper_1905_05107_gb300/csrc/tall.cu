@@ -1,8 +1,10 @@
 // Tall-skinny passes of BLOCK MERGE (Algorithm 2) over the m rows:
 //   TALL_PROJ   : P  = U^T C                              (U_1^T U_2, Eq. 8)
 //   TALL_CGS    : Z  = C - U P;  P2 = U^T Z;  G = Z^T Z    (U_t, second projection)
-//   TALL_QR2    : W  = (C - U P - U P2) M1;  G2 = W^T W     (second CholeskyQR pass)
-//   TALL_UPDATE : U <- U X + C Y                          (U = [U_1 U_o] U_E, truncated)
+//   TALL_QR2    : W  = (C - U P - U P2) M1;  G2 = W^T W     (second CholeskyQR pass;
+//                 W is stored)
+//   TALL_UPDATE : U <- U X + W Y                          (U = [U_1 U_o] U_E, truncated;
+//                 U_o = W R2^{-1}; the ICRS row stage combines C instead of W)
 // plus Y = A^T U (closing refinement of Algorithm 1, ORT probabilities) and
 // the sign-reference dots.
 //
@@ -11,7 +13,7 @@
 // cp.async (16-byte copies when every column start is 16-byte aligned),
 // double-buffered so the next slab streams in while the current one is
 // used.  Every product is a 4x4 register tile fed by 128-bit shared loads:
-// the row-space products (C - U P, Z M1, U X + C Y) tile 4 rows x 4 output
+// the row-space products (C - U P, Z M1, U X + W Y) tile 4 rows x 4 output
 // columns, the Gram-type products (U^T C, Z^T Z) tile 4 x 4 outputs over
 // 4-row chunks.  FP32 tile sums are flushed into FP64 accumulators after
 // every slab.  The CTAs' FP64 partials are summed inside the kernel: the
@@ -461,6 +463,16 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                                   }
                               });
             __syncthreads();
+            if (a.Wout) {
+                // W itself for the UPDATE pass: Q = W R2^{-1} is then formed from
+                // the very W whose Gram gave R2 (explicit CholeskyQR2)
+                const int64_t left = a.m - i0;
+                const int nrow = left < bm ? (int)left : bm;
+                for (int e = tid; e < g * bm; e += bd) {
+                    const int j = e / bm, i = e - j * bm;
+                    if (i < nrow) a.Wout[(int64_t)j * a.ldw + i0 + i] = Ws[(size_t)j * ld + i];
+                }
+            }
             gram_acc<T>(Ws, g, Ws, g, ld, bm, true, acc2, L.c4, red);
         } else {
             const int64_t rows_left = a.m - i0;
@@ -537,8 +549,9 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
             double mx = 0.0;
             for (int w = 0; w < TALL_THREADS / 32; ++w) mx = wmax[w] > mx ? wmax[w] : mx;
             DevState *sw = const_cast<DevState *>(st);
-            sw->robust = mx > 0.1;
-            if (mx > 0.1) sw->robust_rounds += 1;
+            const int rb = sw->robust || mx > 0.1;   // or'ed with the Cholesky's drop test
+            sw->robust = rb;
+            sw->robust_rounds += rb;
         }
     }
 }

@@ -30,7 +30,7 @@ POD_PREC_F32, POD_PREC_BF16, POD_PREC_BF16X3, POD_PREC_TF32X3 = 0, 1, 2, 3
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
             "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
-            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental"]
+            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental", "pod_robust_rounds"]
 
 ROUND_KERNELS = ["sample", "proj", "cgs_gram", "chol1", "qr2_gram", "cgs_robust", "chol1_robust", "qr2_robust",
                  "core_svd", "update", "finish"]
@@ -291,6 +291,12 @@ class Context:
         out = (ctypes.c_double * 4)()
         _check(lib().pod_wedin(self._h, out), "pod_wedin")
         return {"bound": out[0], "norm_R": out[1], "norm_S": out[2], "omega": out[3]}
+
+    def robust_rounds(self) -> int:
+        """Rounds that needed the compensated-Gram rerun of the first CholeskyQR pass."""
+        v = ctypes.c_int32(0)
+        _check(lib().pod_robust_rounds(self._h, ctypes.byref(v)), "pod_robust_rounds")
+        return int(v.value)
 
     def row_draws(self) -> int:
         """w, the row draws per ICRS iteration (0 without rows)."""

@@ -51,3 +51,58 @@ def test_wide_planted(m, n, k, c, dtype, tol):
         assert np.array_equal(g["idx"][t], rec.idx), t
     np.testing.assert_allclose(g["sigma"], ref.sigma, rtol=tol)
     assert O.sin_principal_max(ref.U, g["U"]) <= tol
+
+
+def test_ill_conditioned_blocks_take_the_compensated_rerun():
+    """Raw 200-column blocks of a sigma_i = i^-2 spectrum (condition ~4e4, above
+    the FP32 CholeskyQR2 limit u^-1/2 ~ 4e3): the guarded rerun must trigger,
+    and the result must be as accurate as FP32 passes over the data allow.
+    A backward error of c u sigma_1 moves sigma_i by at most c u sigma_1 and
+    the leading j-dimensional subspace by sin theta_j <= c u sigma_1 /
+    (sigma_j - sigma_{j+1}) (Weyl, Wedin); the bound is taken with c = 10.
+    Without the compensated rerun, dropped pivots of the plain FP32 Gram gave
+    sin theta_10 = 50x that floor and sigma_1 off by up to 60%."""
+    u = 2.0 ** -24
+    A = synth.planted(12000, 1000, 1.0 / np.arange(1, 501) ** 2, 0.0, 73, np.float32)
+    ref = O.isma(A.astype(np.float64), O.Params(k=100, c=200, seed=0x5107, tol=1e-8, refine=False))
+    ctx = pod.Context(to_dev(A), 100, 200, tol=1e-8, refine=False)
+    done, meas, steps = ctx.iterate()
+    assert ctx.robust_rounds() >= 1
+    assert steps == len(ref.trace)
+    for t in range(steps):
+        assert np.array_equal(ctx.trace(t)[0], ref.trace[t].idx)
+    U, s, _ = ctx.modes()
+    ctx.close()
+    s = s.cpu().numpy()
+    U = U.double().cpu().numpy()
+    rs = ref.sigma
+    assert np.all(np.abs(s[:50] - rs[:50]) <= 10 * u * rs[0])
+    for j in (5, 10, 20, 50):
+        assert O.sin_principal_max(ref.U[:, :j], U[:, :j]) <= 10 * u * rs[0] / (rs[j - 1] - rs[j]), j
+
+
+def test_ill_conditioned_refinement_gives_ritz_vectors():
+    """The closing refinement on the same data.  Its input basis is the merged
+    U, whose tail is fixed only to FP32 resolution (sigma_100 - sigma_101 =
+    2e-6 sigma_1), and the Rayleigh-Ritz step mixes that tail into every
+    mode, so the refined modes are checked by their defining properties
+    instead of against the oracle's: they span the merged basis, and Y = A^T U
+    has orthogonal columns of norms sigma (U^T A A^T U = Sigma^2) up to the
+    FP32 rounding of U, |H_ij - delta_ij sigma_i^2| <= c u sigma_1
+    (sigma_i + sigma_j) with c = 10."""
+    u = 2.0 ** -24
+    A = synth.planted(12000, 1000, 1.0 / np.arange(1, 501) ** 2, 0.0, 73, np.float32)
+    A64 = A.astype(np.float64)
+    out = []
+    for refine in (False, True):
+        ctx = pod.Context(to_dev(A), 100, 200, tol=1e-8, refine=refine)
+        ctx.iterate()
+        U, s, _ = ctx.modes()
+        ctx.close()
+        out.append((U.double().cpu().numpy(), s.cpu().numpy()))
+    (U0, _), (U1, s1) = out
+    assert O.sin_principal_max(U0, U1) <= 1e-5
+    Y = A64.T @ U1
+    H = Y.T @ Y
+    bound = 10 * u * s1[0] * (s1[:, None] + s1[None, :])
+    assert np.all(np.abs(H - np.diag(s1 ** 2)) <= bound)
