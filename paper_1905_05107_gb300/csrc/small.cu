@@ -33,68 +33,56 @@ __device__ __forceinline__ double round_to(int dtype, double v) {
 // holds a symmetric Gram matrix in its upper triangle and is overwritten;
 // R (ld) receives the factor with R^T R = G on the kept indices.  A pivot
 // d <= thr (or d <= thrv[k], per index, when thrv is given) marks its index
-// as numerically dependent: R's row is zero
-// (Algorithm 2 drops the matching zero singular values of E).  The row of
-// pivot k is written to R while the trailing update reads the unscaled row
-// from W, so both happen in the same phase.
+// as numerically dependent: R's row is zero (Algorithm 2 drops the matching
+// zero singular values of E).  Every thread forms the pivot's square root
+// and reciprocals itself (no broadcast step).  Threads are laid out as NC
+// columns (a power of two, at least min(n, blockDim)) by blockDim / NC row
+// phases, fixed for the whole factorisation, so the inner loops carry no
+// index division; step k writes row k of R and updates rows i > k, which
+// read only row k.  piv3 is unused (kept for the callers' layouts).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int col_lanes(int n, int bd) {
+    int nc = 32;
+    while (nc < n && nc < bd) nc <<= 1;
+    return nc > bd ? bd : nc;
+}
+
 template <typename X>
 __device__ void chol_drop(X *W, int ldw, int n, X thr, X *R, int ldr, X *piv3, const X *thrv = nullptr) {
+    (void)piv3;
     const int tid = threadIdx.x, bd = blockDim.x;
     for (int e = tid; e < n * n; e += bd) {
         const int i = e / n, j = e % n;
         if (i > j) R[i * ldr + j] = XOps<X>::zero();
     }
-    // piv3 = {sqrt(d), 1/sqrt(d), 1/d} of the current pivot (zeros if dropped),
-    // written by the thread that produces the pivot's final value
-    auto set_pivot = [&](X d, int k) {
-        if (x_gt(d, thrv ? thrv[k] : thr)) {
-            const X p = XOps<X>::sqrt_(d);
-            piv3[0] = p;
-            piv3[1] = XOps<X>::one() / p;
-            piv3[2] = XOps<X>::one() / d;
-        } else {
-            piv3[0] = piv3[1] = piv3[2] = XOps<X>::zero();
-        }
-    };
-    if (tid == 0 && n > 0) set_pivot(W[0], 0);
+    const int NC = col_lanes(n, bd), RS = bd / NC;
+    const int jt = tid & (NC - 1), it = tid / NC;
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        const X piv = piv3[0], inv_piv = piv3[1], inv_d = piv3[2];
-        const bool keep = x_hi(piv) > 0.f;
-        const int rowlen = n - k, w = n - k - 1;
-        X next_d = XOps<X>::zero();
-        bool owner = false;
-        for (int e = tid; e < rowlen + (keep ? w * w : 0); e += bd) {
-            if (e < rowlen) {
-                const int j = k + e;
-                R[k * ldr + j] = keep ? (j == k ? piv : W[k * ldw + j] * inv_piv) : XOps<X>::zero();
-            } else {
-                const int e2 = e - rowlen;
-                const int i = k + 1 + e2 / w, j = k + 1 + e2 % w;
-                if (i <= j) {
-                    const X v = W[i * ldw + j] - (W[k * ldw + i] * W[k * ldw + j]) * inv_d;
-                    W[i * ldw + j] = v;
-                    if (i == k + 1 && j == k + 1) {
-                        next_d = v;
-                        owner = true;
-                    }
-                }
+        const X d = W[k * ldw + k];
+        const bool keep = x_gt(d, thrv ? thrv[k] : thr);
+        X p = XOps<X>::zero(), inv_p = XOps<X>::zero(), inv_d = XOps<X>::zero();
+        if (keep) {
+            p = XOps<X>::sqrt_(d);
+            inv_p = XOps<X>::one() / p;
+            inv_d = inv_p * inv_p;
+        }
+        if (it < RS)
+            for (int j = k + jt; j < n; j += NC) {
+                const X wkj = W[k * ldw + j];
+                if (it == 0) R[k * ldr + j] = keep ? (j == k ? p : wkj * inv_p) : XOps<X>::zero();
+                if (!keep || j == k) continue;
+                const X rkj = wkj * inv_d;
+                for (int i = k + 1 + it; i <= j; i += RS) W[i * ldw + j] = W[i * ldw + j] - W[k * ldw + i] * rkj;
             }
-        }
         __syncthreads();
-        if (k + 1 < n) {
-            // the next pivot: updated above, or unchanged when this pivot was dropped
-            if (keep ? owner : tid == 0) set_pivot(keep ? next_d : W[(k + 1) * ldw + k + 1], k + 1);
-            __syncthreads();
-        }
     }
 }
 
 // M = R^{-1} for upper triangular R, one barrier per row (zero pivots of
 // dropped indices give zero rows and columns of M).  Mw is a work array;
 // row k of M is the scaled row k of Mw, written while the rows above are
-// updated from the unscaled row.
+// updated from the unscaled row.  Same fixed thread layout as chol_drop.
 template <typename X>
 __device__ void tri_inv(const X *R, int ldr, int n, X *Mw, int ldw, X *M, int ldm, X *dinv) {
     const int tid = threadIdx.x, bd = blockDim.x;
@@ -107,17 +95,17 @@ __device__ void tri_inv(const X *R, int ldr, int n, X *Mw, int ldw, X *M, int ld
         const X d = R[k * ldr + k];
         dinv[k] = x_hi(d) != 0.f ? XOps<X>::one() / d : XOps<X>::zero();
     }
+    const int NC = col_lanes(n, bd), RS = bd / NC;
+    const int jt = tid & (NC - 1), it = tid / NC;
     __syncthreads();
     for (int k = n - 1; k >= 0; --k) {
         const X inv = dinv[k];
-        if (x_hi(inv) != 0.f) {
-            const int w = n - k;
-            for (int e = tid; e < w * (k + 1); e += bd) {
-                const int i = e / w, j = k + e % w;
-                if (i == k) M[k * ldm + j] = Mw[k * ldw + j] * inv;
-                else Mw[i * ldw + j] = Mw[i * ldw + j] - R[i * ldr + k] * (Mw[k * ldw + j] * inv);
+        if (x_hi(inv) != 0.f && it < RS)
+            for (int j = k + jt; j < n; j += NC) {
+                const X mkj = Mw[k * ldw + j] * inv;
+                if (it == 0) M[k * ldm + j] = mkj;
+                for (int i = it; i < k; i += RS) Mw[i * ldw + j] = Mw[i * ldw + j] - R[i * ldr + k] * mkj;
             }
-        }
         __syncthreads();
     }
 }
@@ -279,6 +267,133 @@ __device__ int jacobi_hw(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *al
     if (nrow <= 160 && ncol <= 160)
         return jacobi_lp<J, 16, 10>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
     return jacobi_lp<J, 16, 20>(B, ldb, nrow, ncol, V, ldv, alpha, tol, max_sweeps, s_flag);
+}
+
+// Lean FP32 variant for n_c <= 64, same ordering, thresholds and stopping
+// rule as jacobi_lp.  B (and V) have leading dimension 64 with zero rows
+// beyond nrow, so LP lanes hold a column pair as 64 / LP rows per lane with
+// no bounds tests; the pairs of a warp visit their rows in rotated order so
+// that their shared-memory accesses fall in disjoint banks; each lane group
+// keeps its pair indices in registers and advances them by one per round;
+// the rotation uses the fast reciprocal and reciprocal square root (an FP32
+// rotation orthogonal to a few ulp is all the double-float finish needs).
+// V is rotated only when WITHV.
+constexpr int LEAN_LD = 64;
+// lanes per column pair: four (16 rows per lane, 8 pairs per warp) measured
+// fastest of 4, 8 and 16 on the 60-column cores
+constexpr int JLP = 4;
+
+template <int LP, bool WITHV>
+__device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol, int max_sweeps, int *s_flag) {
+    constexpr int E = LEAN_LD / LP, PPW = 32 / LP;
+    const int N = ncol + (ncol & 1), npairs = N / 2, M = N - 1;
+    const int nwork = 32 * ((npairs + PPW - 1) / PPW);
+    const int tid = threadIdx.x;
+    if (tid >= nwork) return 0;
+    const int lane = tid & 31, lp = lane % LP, sub = lane / LP, pr = (tid >> 5) * PPW + sub;
+    const bool active = pr < npairs;
+    int rows[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) rows[e] = lp + LP * ((e + sub) % E);
+    const float tol2 = tol * tol, loose = 16.f * tol, loose2 = loose * loose;
+    int sweep = 0;
+    for (;; ++sweep) {
+        for (int c = tid; c < ncol; c += nwork) {
+            const float4 *bc = reinterpret_cast<const float4 *>(B + (size_t)c * LEAN_LD);
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int i = 0; i < LEAN_LD / 4; i += 2) {
+                const float4 u0 = bc[i], u1 = bc[i + 1];
+                s0 = fmaf(u0.x, u0.x, fmaf(u0.y, u0.y, fmaf(u0.z, u0.z, fmaf(u0.w, u0.w, s0))));
+                s1 = fmaf(u1.x, u1.x, fmaf(u1.y, u1.y, fmaf(u1.z, u1.z, fmaf(u1.w, u1.w, s1))));
+            }
+            alpha[c] = s0 + s1;
+        }
+        if (tid == 0) s_flag[0] = 0;
+        bar_sync_1(nwork);
+        if (sweep >= max_sweeps || ncol < 2) break;
+        // round 0 of the tournament: pair 0 = (M, 0), pair k = (k, M - k)
+        int pa = pr == 0 ? M : pr, qa = pr == 0 ? 0 : M - pr;
+        for (int rnd = 0; rnd < M; ++rnd) {
+            const int p = active ? min(pa, qa) : 0, q = active ? max(pa, qa) : 0;
+            const bool valid = active && q < ncol;
+            float *bp = B + (size_t)p * LEAN_LD, *bq = B + (size_t)(valid ? q : p) * LEAN_LD;
+            float x[E], y[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                x[e] = bp[rows[e]];
+                y[e] = bq[rows[e]];
+            }
+            const float a = alpha[p], b = alpha[valid ? q : p];
+            float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; e += 2) {
+                g0 = fmaf(x[e], y[e], g0);
+                g1 = fmaf(x[e + 1], y[e + 1], g1);
+            }
+            float g = g0 + g1;
+#pragma unroll
+            for (int o = LP / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, LP);
+            if (valid) {
+                const float ab = a * b, g2 = g * g;
+                if (ab > 0.f && g2 > loose2 * ab && lp == 0) s_flag[1] = 1;
+                if (ab > 0.f && g2 > tol2 * ab) {
+                    // the rotation with |theta| <= pi/4 that makes b_p . b_q
+                    // zero: with d = alpha_q - alpha_p, h = 2 g, r = |(d, h)|:
+                    // cos 2theta = |d| / r, cos theta = sqrt((1 + cos 2theta) / 2),
+                    // sin theta = sign(d) h / (2 r cos theta), t = tan theta
+                    const float d = b - a, h = g + g;
+                    const float ir = rsqrtf(fmaf(d, d, h * h));
+                    const float y2 = fmaf(0.5f * fabsf(d), ir, 0.5f);
+                    const float iy = rsqrtf(y2);
+                    const float cs = y2 * iy;
+                    const float sn = copysignf(1.f, d) * (0.5f * h) * (ir * iy);
+                    const float t = sn * iy;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        bp[rows[e]] = fmaf(cs, x[e], -sn * y[e]);
+                        bq[rows[e]] = fmaf(sn, x[e], cs * y[e]);
+                    }
+                    if (WITHV) {
+                        float *vp = V + (size_t)p * LEAN_LD, *vq = V + (size_t)q * LEAN_LD;
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            const float vx = vp[rows[e]], vy = vq[rows[e]];
+                            vp[rows[e]] = fmaf(cs, vx, -sn * vy);
+                            vq[rows[e]] = fmaf(sn, vx, cs * vy);
+                        }
+                    }
+                    if (lp == 0) {
+                        alpha[p] = fmaf(-t, g, a);
+                        alpha[q] = fmaf(t, g, b);
+                        s_flag[0] = 1;
+                    }
+                }
+            }
+            if (pr == 0) {
+                qa = rnd + 1;
+            } else {
+                pa = pa + 1 == M ? 0 : pa + 1;
+                qa = qa + 1 == M ? 0 : qa + 1;
+            }
+            bar_sync_1(nwork);
+        }
+        const int rotated = s_flag[0], big = s_flag[1];
+        bar_sync_1(nwork);
+        if (tid == 0) s_flag[1] = 0;
+        if (!rotated) break;
+        if (!big) {
+            ++sweep;
+            for (int c = tid; c < ncol; c += nwork) {
+                const float *bc = B + (size_t)c * LEAN_LD;
+                float s0 = 0.f;
+                for (int i = 0; i < LEAN_LD; ++i) s0 = fmaf(bc[i], bc[i], s0);
+                alpha[c] = s0;
+            }
+            break;
+        }
+    }
+    return sweep;
 }
 
 // rank of each of n keys in descending order (ties by index) -> order[rank] = i
@@ -523,7 +638,9 @@ __host__ __device__ inline CoreLayout core_layout(int rmax, int cmax, int jsize)
     // FP32 path: 3 X + 8 float g x g arrays; FP64 path: 5 X arrays
     L.phaseA = jsize == 4 ? 3 * al16x((size_t)cmax * cmax * 8) + 8 * al16x((size_t)cmax * cmax * 4)
                           : 5 * al16x((size_t)cmax * cmax * 8);
-    L.phaseB = 2 * al16x((size_t)nmax * nmax * jsize) + al16x((size_t)nmax * jsize) + al16x((size_t)nmax * 4);
+    // B, V: leading dimension 64 (zero-padded rows) on the lean FP32 path (n_c <= 64)
+    const size_t jb = (jsize == 4 && nmax <= LEAN_LD) ? (size_t)LEAN_LD * nmax : (size_t)nmax * nmax;
+    L.phaseB = 2 * al16x(jb * jsize) + al16x((size_t)nmax * jsize) + al16x((size_t)nmax * 4);
     // Vr, Q, Yt: nmax x rmax X; Gb, Rb, Mw, Mb: rmax x rmax X; Bs: nmax x rmax J;
     // BtB: rmax^2 J; xv, yv: rmax J; sig: rmax X; ord2: rmax int
     L.phaseC = 3 * al16x((size_t)nmax * rmax * 8) + 4 * al16x((size_t)rmax * rmax * 8) +
@@ -760,8 +877,10 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     // ---- phase B: Jacobi on the rows of E: B = E^T (column p = row p of E)
     // (wide cores: B, V in shared memory when they fit, else in global scratch)
     Carve cvB{(gbase && a.jac_smem) ? smem_raw : work};
-    J *B = cvB.take<J>((size_t)nmax * nmax);
-    J *V = cvB.take<J>((size_t)nmax * nmax);
+    const bool lean = sizeof(J) == 4 && nmax <= LEAN_LD;
+    const int ldj = lean ? LEAN_LD : nc;   // leading dimension of B and V
+    J *B = cvB.take<J>(lean ? (size_t)LEAN_LD * nmax : (size_t)nmax * nmax);
+    J *V = cvB.take<J>(lean ? (size_t)LEAN_LD * nmax : (size_t)nmax * nmax);
     J *alpha = cvB.take<J>(nmax);
     int *order = cvB.take<int>(nmax);
     Carve cv = (gbase && a.jac_smem) ? Carve{work} : cvB;
@@ -779,11 +898,26 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     X *sig = cv.take<X>(a.rmax);
     int *ord2 = cv.take<int>(a.rmax);
     const bool f32 = sizeof(J) == 4;
-    for (int e = tid; e < nc * nc; e += bd) {
-        const int col = e / nc, i = e % nc;   // B column col = row col of E; entry i = E[col][i]
-        B[col * nc + i] = (J)x_hi(Ex[i * nc + col]) + (J)(f32 ? 0.f : (float)0);
-        if (!f32) B[col * nc + i] = (J)XOps<X>::to(Ex[i * nc + col]);
-        V[col * nc + i] = (i == col) ? (J)1 : (J)0;
+    // lean path: B scaled by a power of two to max |B_ij| in [1/2, 1), so the
+    // FP32 squared norms and their products stay clear of overflow and
+    // underflow (rotations and the directions the finish uses are unchanged)
+    double jscale = 1.0;
+    if (lean) {
+        double mx = 0.0;
+        for (int e = tid; e < nc * nc; e += bd) mx = fmax(mx, fabs((double)x_hi(Ex[e])));
+        mx = block_max<double>(mx, red);
+        if (mx > 0.0 && isfinite(mx)) {
+            int ex;
+            frexp(mx, &ex);
+            jscale = ldexp(1.0, -ex);
+        }
+    }
+    for (int e = tid; e < nc * ldj; e += bd) {
+        const int col = e / ldj, i = e % ldj;   // B column col = row col of E; entry i = E[col][i]
+        J v = (J)0;
+        if (i < nc) v = f32 ? (J)((double)x_hi(Ex[i * nc + col]) * jscale) : (J)XOps<X>::to(Ex[i * nc + col]);
+        B[col * ldj + i] = v;
+        V[col * ldj + i] = (i == col) ? (J)1 : (J)0;
     }
     __syncthreads();
     const J eps_j = f32 ? (J)1.1920928955078125e-07 : (J)2.220446049250313e-16;
@@ -793,7 +927,14 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     const J tol = f32 ? (J)2 * sqrt((J)nc) * eps_j : (J)nc * eps_j;
     clk[1] = clock64();
     if (tid == 0) s_flag[1] = 0;
-    const int nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, f32 ? 20 : 30, s_flag);
+    int nsweeps;
+    if constexpr (sizeof(J) == 4) {
+        if (lean && a.tape) nsweeps = jacobi_lean<JLP, true>(B, nc, V, alpha, tol, 20, s_flag);
+        else if (lean) nsweeps = jacobi_lean<JLP, false>(B, nc, V, alpha, tol, 20, s_flag);
+        else nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 20, s_flag);
+    } else {
+        nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 30, s_flag);
+    }
     __syncthreads();
     clk[2] = clock64();
     sort_desc<J>(alpha, nc, order);
@@ -808,7 +949,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         // then sigma_s = |E^T q_s| (Rayleigh quotient).
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
-            const J *bs = B + (size_t)order[s] * nc;
+            const J *bs = B + (size_t)order[s] * ldj;
             X acc = XOps<X>::zero();
             for (int j = 0; j < nc; ++j) acc = acc + Ex[j * nc + p] * XOps<X>::from_f((float)bs[j]);
             Vr[s * nc + p] = acc;
@@ -857,7 +998,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     } else {
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
-            Q[s * nc + p] = XOps<X>::from((double)V[order[s] * nc + p]);
+            Q[s * nc + p] = XOps<X>::from((double)V[order[s] * ldj + p]);
         }
         for (int s = tid; s < rsel; s += bd) sig[s] = XOps<X>::from(sqrt((double)alpha[order[s]]));
         __syncthreads();
@@ -922,12 +1063,12 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
             tp[3] = nc;
         }
         for (int s = tid; s < nc; s += bd)
-            tp[TL.sig + s] = s < rsel ? XOps<X>::to(sig[s]) : sqrt((double)alpha[order[s]]);
+            tp[TL.sig + s] = s < rsel ? XOps<X>::to(sig[s]) : sqrt((double)alpha[order[s]]) / jscale;
         for (int e = tid; e < nc * nc; e += bd) {
             const int q = e / nc, p = e % nc;
             tp[TL.E + (int64_t)q * nmax + p] = XOps<X>::to(Ex[q * nc + p]);
             tp[TL.UE + (int64_t)q * nmax + p] =
-                q < rsel ? XOps<X>::to(Q[q * nc + p]) : (double)V[(size_t)order[q] * nc + p];
+                q < rsel ? XOps<X>::to(Q[q * nc + p]) : (double)V[(size_t)order[q] * ldj + p];
         }
         for (int e = tid; e < r * g; e += bd) {
             const int l = e / g, j = e % g;
