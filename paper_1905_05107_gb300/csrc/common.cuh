@@ -199,10 +199,21 @@ template <> struct XOps<dfloat> {
     __device__ static dfloat one() { return {1.f, 0.f}; }
 };
 
+template <> struct XOps<float> {
+    __device__ static float from(double d) { return (float)d; }
+    __device__ static float from_f(float f) { return f; }
+    __device__ static double to(float x) { return (double)x; }
+    __device__ static float sqrt_(float x) { return sqrtf(x); }
+    __device__ static float zero() { return 0.f; }
+    __device__ static float one() { return 1.f; }
+};
+
+__device__ __forceinline__ bool x_gt(float a, float b) { return a > b; }
 __device__ __forceinline__ bool x_gt(double a, double b) { return a > b; }
 __device__ __forceinline__ bool x_gt(dfloat a, dfloat b) {
     return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
 }
+__device__ __forceinline__ float x_hi(float a) { return a; }
 __device__ __forceinline__ float x_hi(double a) { return (float)a; }
 __device__ __forceinline__ float x_hi(dfloat a) { return a.hi; }
 // Rotation arithmetic of the Jacobi sweeps: fast reciprocals on the FP32

@@ -511,7 +511,13 @@ pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t
 // dropping, M1 = fl(R1^{-1}) (the matrix the tall pass applies), and
 // R1p = M1^{-1} (the exact inverse of what was applied, used in E).
 // ---------------------------------------------------------------------------
-template <typename X>
+//
+// XC is the arithmetic of the Cholesky and of M1: FP32 in the plain pass of
+// FP32 data, whose Gram is only FP32-accurate anyway (M1 is rounded to FP32
+// before use, so an FP32 inverse costs no accuracy: both errors are
+// O(u kappa)); X (double-float or FP64) in the compensated rerun and for FP64
+// data.  R1p, the inverse of the applied M1, is always formed in X.
+template <typename X, typename XC>
 __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     DevState *st = a.st;
     if (st->done) return;
@@ -525,9 +531,13 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     X *Mw = cv.take<X>((size_t)ld * ld);
     X *M = cv.take<X>((size_t)ld * ld);
     __shared__ double red[32];
-    __shared__ X piv3[3];
+    __shared__ XC piv3[3];
     X *dinv = cv.take<X>(ld);
-    X *thrv = cv.take<X>(ld);
+    X *thrv_x = cv.take<X>(ld);
+    // the XC stage lives in the same arrays (XC is no wider than X)
+    XC *Wc = reinterpret_cast<XC *>(W), *Rc = reinterpret_cast<XC *>(R);
+    XC *Mwc = reinterpret_cast<XC *>(Mw), *Mc = reinterpret_cast<XC *>(M);
+    XC *dinvc = reinterpret_cast<XC *>(dinv), *thrv = reinterpret_cast<XC *>(thrv_x);
     const int tid = threadIdx.x, bd = blockDim.x;
     const double *P2 = a.PG;
     const double *G = a.PG + (int64_t)a.rmax * a.cmax;
@@ -555,18 +565,18 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     const bool f32 = a.dtype == POD_F32;
     const double eps = f32 ? 8.0 * u : nc * u;
     const double floor_abs = eps * eps * scale;
-    const X thr = XOps<X>::from(floor_abs);
+    const XC thr = XOps<XC>::from(floor_abs);
     const bool plain32 = f32 && !a.cond;
     for (int j = tid; j < g; j += bd) {
         const double tj = 8.0 * u * G[j * ld + j];
-        thrv[j] = XOps<X>::from(plain32 && tj > floor_abs ? tj : floor_abs);
+        thrv[j] = XOps<XC>::from(plain32 && tj > floor_abs ? tj : floor_abs);
     }
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
-        W[i * ld + j] = XOps<X>::from(i <= j ? G[i * ld + j] : 0.0);
+        Wc[i * ld + j] = XOps<XC>::from(i <= j ? G[i * ld + j] : 0.0);
     }
     __syncthreads();
-    chol_drop<X>(W, ld, g, thr, R, ld, piv3, thrv);
+    chol_drop<XC>(Wc, ld, g, thr, Rc, ld, piv3, thrv);
     if (!a.cond) {
         // a column the plain FP32 pass dropped under its noise floor
         // 8 u G_jj may hide more than 8 u sigma_1: the round then takes the
@@ -575,20 +585,21 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
         int flag = 0;
         if (plain32)
             for (int j = tid; j < g; j += bd)
-                if (x_hi(R[j * ld + j]) == 0.f && 8.0 * u * G[j * ld + j] > floor_abs) flag = 1;
+                if (x_hi(Rc[j * ld + j]) == 0.f && 8.0 * u * G[j * ld + j] > floor_abs) flag = 1;
         flag = __syncthreads_or(flag);
         if (tid == 0) st->robust = flag;
     }
-    tri_inv<X>(R, ld, g, Mw, ld, M, ld, dinv);
-    // round M1 to the storage type: that is the matrix the QR2 pass applies
+    tri_inv<XC>(Rc, ld, g, Mwc, ld, Mc, ld, dinvc);
+    // round M1 to the storage type: that is the matrix the QR2 pass applies;
+    // its X copy goes to R's array (the XC factor is no longer needed)
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
-        const double v = round_to(a.dtype, XOps<X>::to(M[i * ld + j]));
+        const double v = round_to(a.dtype, XOps<XC>::to(Mc[i * ld + j]));
         a.M1[i * ld + j] = v;
-        M[i * ld + j] = XOps<X>::from(v);
+        R[i * ld + j] = XOps<X>::from(v);
     }
     __syncthreads();
-    tri_inv<X>(M, ld, g, Mw, ld, W, ld, dinv);
+    tri_inv<X>(R, ld, g, Mw, ld, W, ld, dinv);
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
         a.R1p[i * ld + j] = XOps<X>::to(W[i * ld + j]);
@@ -600,12 +611,15 @@ size_t small_chol_smem(int cmax) { return 4 * al16x((size_t)cmax * cmax * 8) + 2
 pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s) {
     const size_t smem = a.gws_chol ? 64 : small_chol_smem(a.cmax);
     if (smem > 220 * 1024) return POD_EUNSUPPORTED;
-    if (a.dtype == POD_F32) {
-        POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_small_chol<dfloat><<<1, CHOL_THREADS, smem, s>>>(a);
+    if (a.dtype == POD_F32 && !a.cond) {
+        POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<dfloat, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_small_chol<dfloat, float><<<1, CHOL_THREADS, smem, s>>>(a);
+    } else if (a.dtype == POD_F32) {
+        POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<dfloat, dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_small_chol<dfloat, dfloat><<<1, CHOL_THREADS, smem, s>>>(a);
     } else {
-        POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_small_chol<double><<<1, CHOL_THREADS, smem, s>>>(a);
+        POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_small_chol<double, double><<<1, CHOL_THREADS, smem, s>>>(a);
     }
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;

@@ -97,11 +97,34 @@ struct AllLive {
 };
 
 // ------------------------------------------------------------ micro-kernels
+// Cross-slab accumulators of the Gram-type products.  FP32 data: each 8-byte
+// slot holds a double-float (hi, lo) pair updated with TwoSum (FP32 pipes;
+// an FP64 add per output and slab cost as much FP64-pipe time as the slab's
+// FP32 products, FP64 running ~58x slower than FP32 here); FP64 data: a
+// plain double.  acc_read gives the slot's value as a double.
+__device__ __forceinline__ void acc_add(double *slot, float s) {
+    float2 *p = reinterpret_cast<float2 *>(slot);
+    const float2 v = *p;
+    const dfloat t = df_two_sum(v.x, s);
+    const dfloat n = df_fast_two_sum(t.hi, t.lo + v.y);
+    *p = make_float2(n.hi, n.lo);
+}
+__device__ __forceinline__ void acc_add(double *slot, double s) { *slot += s; }
+template <typename T>
+__device__ __forceinline__ double acc_read(const double *slot) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = *reinterpret_cast<const float2 *>(slot);
+        return (double)v.x + (double)v.y;
+    } else {
+        return *slot;
+    }
+}
+
 // acc[p][q] += sum_i X[p][i] Y[q][i] over the bm rows of a slab (X, Y
 // column-major with leading dimension ld; p < na, q < nb).  Tiles of 4x4
-// outputs over 4-row chunks; tiles with ti > tj skipped when sym.  acc is
-// FP64 with leading dimension ldacc; red holds blockDim*16 T.  Ends with a
-// barrier.
+// outputs over 4-row chunks; tiles with ti > tj skipped when sym.  acc has
+// leading dimension ldacc (slots as in acc_add); red holds blockDim*16 T.
+// Ends with a barrier.
 template <typename T>
 __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm, bool sym, double *acc,
                          int ldacc, T *red) {
@@ -132,7 +155,7 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[(4 * ti + u) * ldacc + 4 * tj + v] += (double)a[u * 4 + v];
+                for (int v = 0; v < 4; ++v) acc_add(&acc[(4 * ti + u) * ldacc + 4 * tj + v], a[u * 4 + v]);
         }
         __syncthreads();
         return;
@@ -169,7 +192,7 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
         if (sym && i2 > j2) continue;
         T s = (T)0;
         for (int g2 = 0; g2 < RG; ++g2) s += red[(g2 * nT + t2) * 16 + uv];
-        acc[(4 * i2 + (uv >> 2)) * ldacc + 4 * j2 + (uv & 3)] += (double)s;
+        acc_add(&acc[(4 * i2 + (uv >> 2)) * ldacc + 4 * j2 + (uv & 3)], s);
     }
     __syncthreads();
 }
@@ -177,7 +200,8 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 // As gram_acc for a symmetric X^T X with every product split exactly
 // (TwoProduct) and summed with TwoSum: the tile sums carry ~44 bits before the
 // FP64 flush.  Used for the first CholeskyQR Gram when the plain FP32 one
-// proved too inexact (ill-conditioned residual blocks).  Ends with a barrier.
+// proved too inexact (ill-conditioned residual blocks).  Its acc slots are
+// plain doubles (FP64 running sums).  Ends with a barrier.
 template <typename T>
 __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, int ldacc) {
     const int ta = (na + 3) >> 2, nT = ta * ta, chunks = bm >> 2;
@@ -505,22 +529,23 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     if (KIND == TALL_PROJ) {
         for (int e = tid; e < r * g; e += bd) {
             const int l = e / g, j = e - l * g;
-            out[l * a.cmax + j] = acc1[l * L.c4 + j];
+            out[l * a.cmax + j] = acc_read<T>(&acc1[l * L.c4 + j]);
         }
     } else if (KIND == TALL_CGS) {
         for (int e = tid; e < r * g; e += bd) {
             const int l = e / g, j = e - l * g;
-            out[l * a.cmax + j] = acc1[l * L.c4 + j];
+            out[l * a.cmax + j] = acc_read<T>(&acc1[l * L.c4 + j]);
         }
         double *outG = out + (int64_t)a.rmax * a.cmax;
         for (int e = tid; e < g * g; e += bd) {
             const int p = e / g, q = e - p * g;
-            if (p <= q) outG[p * a.cmax + q] = acc2[p * L.c4 + q];
+            // the compensated Gram of the rerun keeps FP64 running sums
+            if (p <= q) outG[p * a.cmax + q] = a.cond ? acc2[p * L.c4 + q] : acc_read<T>(&acc2[p * L.c4 + q]);
         }
     } else {
         for (int e = tid; e < g * g; e += bd) {
             const int p = e / g, q = e - p * g;
-            if (p <= q) out[p * a.cmax + q] = acc2[p * L.c4 + q];
+            if (p <= q) out[p * a.cmax + q] = acc_read<T>(&acc2[p * L.c4 + q]);
         }
     }
     const bool last = tall_reduce(a.part, a.gsum, a.out, (int)a.part_stride, a.part_stride, a.counters, s_flag);
@@ -622,7 +647,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_atu(AtuArgs<T> a, int nb, int 
     double *out = a.part + (int64_t)blockIdx.y * a.n * a.rmax;
     for (int e = tid; e < ncols * r; e += bd) {
         const int l = e / ncols, c = e - l * ncols;
-        out[(int64_t)l * a.n + j0 + c] = acc[c * r4 + l];
+        out[(int64_t)l * a.n + j0 + c] = acc_read<T>(&acc[c * r4 + l]);
     }
     // the last of the `split` CTAs of this column block sums them
     __threadfence();
