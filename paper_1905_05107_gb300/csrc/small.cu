@@ -742,14 +742,23 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         dev = block_max<double>(dev, red);
         dmax = block_max<double>(dmax, red);
         if (dev < 0.1) {
+            // Newton from I: the residual after n steps is ~ dev^(2^n), so
+            // take the first n <= 3 with dev^(2^n) <= u / 4
+            const double d2 = dev * dev;
+            const int nit = d2 <= 0.25 * u ? 1 : (d2 * d2 <= 0.25 * u ? 2 : 3);
+            // step 1 for R2 from R2 = I (on the kept indices): T1 = G2 - I
             for (int e = tid; e < g * g; e += bd) {
                 const int i = e / g, j = e % g;
-                const bool kept = Gf[i * ld + i] != 0.f;
-                R2f[i * ld + j] = (i == j && kept) ? 1.f : 0.f;
-                M2f[i * ld + j] = (i == j && kept) ? 1.f : 0.f;
+                const bool kept = Gf[i * ld + i] != 0.f && Gf[j * ld + j] != 0.f;
+                float v = 0.f;
+                if (i <= j && kept) {
+                    const float t = Gf[i * ld + j] - (i == j ? 1.f : 0.f);
+                    v = (i == j ? 1.f : 0.f) + (i == j ? 0.5f * t : t);
+                }
+                R2f[i * ld + j] = v;
             }
             __syncthreads();
-            for (int it = 0; it < 3; ++it) {
+            for (int it = 1; it < nit; ++it) {
                 // T1 = G2 - R2^T R2 (upper part)
                 for (int e = tid; e < g * g; e += bd) {
                     const int i = e / g, j = e % g;
@@ -769,14 +778,24 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
                 }
                 __syncthreads();
             }
-            for (int it = 0; it < 3; ++it) {
-                // T1 = 2I - R2 M2 ; M2 <- M2 T1   (all upper triangular)
+            // M2 = R2^{-1}: X <- X (2I - R2 X) from X = I (first step 2I - R2),
+            // the iterates alternating between M2f and the unused M2x storage
+            float *Ma = M2f, *Mb = reinterpret_cast<float *>(M2x);
+            for (int e = tid; e < g * g; e += bd) {
+                const int i = e / g, j = e % g;
+                float v = 0.f;
+                if (i <= j) v = (i == j && Gf[i * ld + i] != 0.f ? 2.f : 0.f) - R2f[i * ld + j];
+                Ma[i * ld + j] = v;
+            }
+            __syncthreads();
+            for (int it = 1; it < nit; ++it) {
+                // T1 = 2I - R2 Ma ; Mb = Ma T1   (all upper triangular)
                 for (int e = tid; e < g * g; e += bd) {
                     const int i = e / g, j = e % g;
                     float v = 0.f;
                     if (i <= j) {
                         float acc = 0.f;
-                        for (int l = i; l <= j; ++l) acc = fmaf(R2f[i * ld + l], M2f[l * ld + j], acc);
+                        for (int l = i; l <= j; ++l) acc = fmaf(R2f[i * ld + l], Ma[l * ld + j], acc);
                         v = (i == j && Gf[i * ld + i] != 0.f ? 2.f : 0.f) - acc;
                     }
                     T1[i * ld + j] = v;
@@ -786,13 +805,15 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
                     const int i = e / g, j = e % g;
                     float v = 0.f;
                     if (i <= j)
-                        for (int l = i; l <= j; ++l) v = fmaf(M2f[i * ld + l], T1[l * ld + j], v);
-                    Rf[i * ld + j] = v;   // scratch
+                        for (int l = i; l <= j; ++l) v = fmaf(Ma[i * ld + l], T1[l * ld + j], v);
+                    Mb[i * ld + j] = v;
                 }
                 __syncthreads();
-                for (int e = tid; e < g * g; e += bd) M2f[(e / g) * ld + e % g] = Rf[(e / g) * ld + e % g];
-                __syncthreads();
+                float *tmp = Ma;
+                Ma = Mb;
+                Mb = tmp;
             }
+            M2f = Ma;
         } else {
             const double eps = nc * u;
             const X thr = XOps<X>::from(eps * eps * dmax);
