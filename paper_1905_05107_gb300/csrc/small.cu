@@ -741,11 +741,23 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         }
         dev = block_max<double>(dev, red);
         dmax = block_max<double>(dmax, red);
-        if (dev < 0.1) {
-            // Newton from I: the residual after n steps is ~ dev^(2^n), so
-            // take the first n <= 3 with dev^(2^n) <= u / 4
-            const double d2 = dev * dev;
-            const int nit = d2 <= 0.25 * u ? 1 : (d2 * d2 <= 0.25 * u ? 2 : 3);
+        // Newton steps from I.  For R2 (R <- R + T(G2 - R^T R)) the error
+        // contracts by ~2 dev per step (linear), after n steps ~(2 dev)^(n+1);
+        // for M2 (X <- X (2I - R2 X)) it squares, ~(2 dev)^(2^n).  Each takes
+        // the fewest steps that reach u; beyond dev = 1.5e-2 the double-float
+        // Cholesky runs instead.
+        int nitR = 0, nitM = 0;
+        {
+            const double d = 2.0 * dev;
+            double pr = d * d, pm = d * d;
+            nitR = 1;
+            while (pr > u && nitR < 4) { pr *= d; ++nitR; }
+            nitM = 1;
+            while (pm > u && nitM < 4) { pm *= pm; ++nitM; }
+            if (pr > u) nitR = 0;
+        }
+        if (nitR > 0) {
+            const int nit = nitR;
             // step 1 for R2 from R2 = I (on the kept indices): T1 = G2 - I
             for (int e = tid; e < g * g; e += bd) {
                 const int i = e / g, j = e % g;
@@ -788,7 +800,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
                 Ma[i * ld + j] = v;
             }
             __syncthreads();
-            for (int it = 1; it < nit; ++it) {
+            for (int it = 1; it < nitM; ++it) {
                 // T1 = 2I - R2 Ma ; Mb = Ma T1   (all upper triangular)
                 for (int e = tid; e < g * g; e += bd) {
                     const int i = e / g, j = e % g;
@@ -990,16 +1002,123 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
             Vr[s * nc + p] = acc;
         }
         __syncthreads();
+        const int rm = a.rmax;
         for (int e = tid; e < rsel * rsel; e += bd) {
             const int i = e / rsel, j = e % rsel;
             X acc = XOps<X>::zero();
             if (i <= j)
                 for (int p = 0; p < nc; ++p) acc = acc + Vr[i * nc + p] * Vr[j * nc + p];
-            Gb[i * a.rmax + j] = acc;
+            Gb[i * rm + j] = acc;
         }
         __syncthreads();
-        chol_drop<X>(Gb, a.rmax, rsel, XOps<X>::from(1e-60), Rb, a.rmax, piv3);
-        tri_inv<X>(Rb, a.rmax, rsel, Mw, a.rmax, Mb, a.rmax, dinv);
+        // CholeskyQR of Vr.  Its columns are nearly orthogonal (the rotated
+        // rows' couplings are below the Jacobi threshold and the power step
+        // only damps them), so with D = diag(Gb) and Gs = D^{-1/2} Gb D^{-1/2}
+        // = I + F the factor Rs of Gs and Rs^{-1} come from Newton steps from
+        // I, as in phase A, to the double-float unit (2^-44); a larger |F|
+        // takes the Cholesky.  Mb = D^{-1/2} Rs^{-1}, so Q = Vr Mb.
+        double fm = 0.0;
+        for (int e = tid; e < rsel * rsel; e += bd) {
+            const int i = e / rsel, j = e % rsel;
+            if (i < j) {
+                const double di = XOps<X>::to(Gb[i * rm + i]), dj = XOps<X>::to(Gb[j * rm + j]);
+                if (di > 1e-60 && dj > 1e-60) fm = fmax(fm, fabs(XOps<X>::to(Gb[i * rm + j])) / sqrt(di * dj));
+            }
+        }
+        for (int i = tid; i < rsel; i += bd) {
+            const X d = Gb[i * rm + i];
+            dinv[i] = XOps<X>::to(d) > 1e-60 ? XOps<X>::one() / XOps<X>::sqrt_(d) : XOps<X>::zero();
+        }
+        fm = block_max<double>(fm, red);
+        const double ud = 5.684341886080802e-14;   // 2^-44
+        int nR = 0, nM = 0;
+        {
+            const double d = 2.0 * fm;
+            double pr = d * d, pm = d * d;
+            nR = 1;
+            while (pr > ud && nR < 4) { pr *= d; ++nR; }
+            nM = 1;
+            while (pm > ud && nM < 4) { pm *= pm; ++nM; }
+            if (pr > ud) nR = 0;
+        }
+        if (nR > 0) {
+            auto kept = [&](int i) { return x_hi(dinv[i]) != 0.f; };
+            for (int e = tid; e < rsel * rsel; e += bd) {
+                const int i = e / rsel, j = e % rsel;
+                if (i <= j) Gb[i * rm + j] = kept(i) && kept(j) ? Gb[i * rm + j] * dinv[i] * dinv[j] : XOps<X>::zero();
+            }
+            __syncthreads();
+            // Rs = I + T(Gs - I), then Rs <- Rs + T(Gs - Rs^T Rs)
+            for (int e = tid; e < rsel * rsel; e += bd) {
+                const int i = e / rsel, j = e % rsel;
+                X v = XOps<X>::zero();
+                if (i <= j && kept(i) && kept(j)) {
+                    const X t = Gb[i * rm + j] - (i == j ? XOps<X>::one() : XOps<X>::zero());
+                    v = i == j ? XOps<X>::one() + t * XOps<X>::from(0.5) : t;
+                }
+                Rb[i * rm + j] = v;
+            }
+            __syncthreads();
+            for (int it = 1; it < nR; ++it) {
+                for (int e = tid; e < rsel * rsel; e += bd) {
+                    const int i = e / rsel, j = e % rsel;
+                    X v = XOps<X>::zero();
+                    if (i <= j) {
+                        v = Gb[i * rm + j];
+                        for (int l = 0; l <= i; ++l) v = v - Rb[l * rm + i] * Rb[l * rm + j];
+                    }
+                    Mw[i * rm + j] = v;
+                }
+                __syncthreads();
+                for (int e = tid; e < rsel * rsel; e += bd) {
+                    const int i = e / rsel, j = e % rsel;
+                    if (i <= j && kept(i) && kept(j))
+                        Rb[i * rm + j] = Rb[i * rm + j] + (i == j ? Mw[i * rm + j] * XOps<X>::from(0.5) : Mw[i * rm + j]);
+                }
+                __syncthreads();
+            }
+            // Rs^{-1}: X <- X (2I - Rs X) from X = I, alternating Mb / Gb
+            X *Ma = Mb, *Mc = Gb;
+            for (int e = tid; e < rsel * rsel; e += bd) {
+                const int i = e / rsel, j = e % rsel;
+                X v = XOps<X>::zero();
+                if (i <= j) v = (i == j && kept(i) ? XOps<X>::from(2.0) : XOps<X>::zero()) - Rb[i * rm + j];
+                Ma[i * rm + j] = v;
+            }
+            __syncthreads();
+            for (int it = 1; it < nM; ++it) {
+                for (int e = tid; e < rsel * rsel; e += bd) {
+                    const int i = e / rsel, j = e % rsel;
+                    X v = XOps<X>::zero();
+                    if (i <= j) {
+                        X acc = XOps<X>::zero();
+                        for (int l = i; l <= j; ++l) acc = acc + Rb[i * rm + l] * Ma[l * rm + j];
+                        v = (i == j && kept(i) ? XOps<X>::from(2.0) : XOps<X>::zero()) - acc;
+                    }
+                    Mw[i * rm + j] = v;
+                }
+                __syncthreads();
+                for (int e = tid; e < rsel * rsel; e += bd) {
+                    const int i = e / rsel, j = e % rsel;
+                    X v = XOps<X>::zero();
+                    if (i <= j)
+                        for (int l = i; l <= j; ++l) v = v + Ma[i * rm + l] * Mw[l * rm + j];
+                    Mc[i * rm + j] = v;
+                }
+                __syncthreads();
+                X *tmp = Ma;
+                Ma = Mc;
+                Mc = tmp;
+            }
+            for (int e = tid; e < rsel * rsel; e += bd) {
+                const int i = e / rsel, j = e % rsel;
+                Mb[i * rm + j] = i <= j ? dinv[i] * Ma[i * rm + j] : XOps<X>::zero();
+            }
+            __syncthreads();
+        } else {
+            chol_drop<X>(Gb, rm, rsel, XOps<X>::from(1e-60), Rb, rm, piv3);
+            tri_inv<X>(Rb, rm, rsel, Mw, rm, Mb, rm, dinv);
+        }
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
             X acc = XOps<X>::zero();
