@@ -1,0 +1,103 @@
+"""Row-sharded ISMA on torch.distributed ranks (test infrastructure).
+
+The multi-GPU design of the hot path shards the rows of A (and of U) across
+ranks: every rank holds rows [m0, m1) of every column.  Each step then needs
+one exchange, a fixed-order sum of small partials:
+
+* column squared norms (Eq. 2): local partials of s, summed (n values);
+* the draws (Algorithm 1, GET UPDATE) are replicated: every rank computes the
+  same integer weights from the same s and the same Philox counters, so no
+  broadcast is needed;
+* BLOCK MERGE (Algorithm 2): P = U^T C, the second projection P2 = U^T Z and
+  the two CholeskyQR Grams G1 = Z^T Z, G2 = W^T W are local partials summed
+  across ranks; the Cholesky factors, the core E (Eq. 8) and its SVD (Eq. 9)
+  are replicated; U is updated on local rows only;
+* ORT values (Eq. 6) and the closing refinement need A^T U: local partials
+  summed (n x r);
+* the sign reference of the output modes: local dots summed.
+
+The arithmetic is FP64 NumPy, the same steps the CUDA kernels take (CGS2 and
+CholeskyQR2 for the residual block, explicit Q = Z R1^{-1} R2^{-1}), written
+here only to check that the sharded exchanges reproduce the single-rank
+result.  The sampling helpers are the oracle's; nothing here is imported by
+the library.
+"""
+import numpy as np
+import torch
+import torch.distributed as dist
+
+from oracle import isma as O
+
+
+def allreduce(x: np.ndarray) -> np.ndarray:
+    """Sum of a FP64 array over all ranks (gloo all_reduce)."""
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.numpy()
+
+
+def merge_sharded(U: np.ndarray, s1: np.ndarray, C: np.ndarray, r: int, m_global: int):
+    """BLOCK MERGE with local rows of U and C (Algorithm 2, Eqs. 8-9)."""
+    r1, g = U.shape[1], C.shape[1]
+    P = allreduce(U.T @ C)
+    Z = C - U @ P
+    P2 = allreduce(U.T @ Z)
+    Z = Z - U @ P2
+    G1 = allreduce(Z.T @ Z)
+    R1 = np.linalg.cholesky(G1).T
+    W = np.linalg.solve(R1.T, Z.T).T          # Z R1^{-1}
+    G2 = allreduce(W.T @ W)
+    R2 = np.linalg.cholesky(G2).T
+    Q = np.linalg.solve(R2.T, W.T).T          # W R2^{-1}
+    E = np.zeros((r1 + g, r1 + g))
+    E[:r1, :r1] = np.diag(s1)
+    E[:r1, r1:] = P + P2
+    E[r1:, r1:] = R2 @ R1
+    UE, sE, _ = np.linalg.svd(E)
+    if sE.size == 0 or sE[0] == 0:
+        keep = 0
+    else:
+        thresh = max(m_global, r1 + g) * np.finfo(np.float64).eps * sE[0]
+        keep = min(r, int(np.count_nonzero(sE > thresh)))
+    Unew = np.hstack([U, Q]) @ UE[:, :keep]
+    return Unew, sE[:keep].copy(), UE
+
+
+def isma_sharded(A_local: np.ndarray, m_global: int, row0: int, p: "O.Params"):
+    """Algorithm 1 on this rank's rows; returns (local U, sigma, draws per
+    round, measures per round)."""
+    n = A_local.shape[1]
+    r = p.carried_rank()
+    s = allreduce(np.einsum("ij,ij->j", A_local, A_local))
+    in_S = np.ones(n, dtype=bool)
+    U = np.zeros((A_local.shape[0], 0))
+    sig = np.zeros(0)
+    draws, measures = [], []
+    t = 0
+    while True:
+        if t > 0 and p.col_strategy == "ort":
+            Y = allreduce(A_local.T @ U)
+            vals = np.maximum(0.0, s - np.sum(Y * Y, axis=1))
+        else:
+            vals = O.column_values("l2n" if t == 0 else p.col_strategy, t, s, None, None)
+        idx, _ = O.sample_columns(vals, in_S, p.c, p.seed, t)
+        in_S[idx] = False
+        r_prev = U.shape[1]
+        U, sig, UE = merge_sharded(U, sig, A_local[:, idx], r, m_global)
+        sin_max, _ = O.convergence_measures(UE, p.k, r_prev)
+        draws.append(idx)
+        measures.append(sin_max)
+        t += 1
+        if (t > 1 and r_prev >= p.k and sin_max <= p.tol) or not in_S.any():
+            break
+    if p.refine and U.shape[1] > 0:
+        Y = allreduce(A_local.T @ U)
+        _, R = np.linalg.qr(Y, mode="reduced")
+        _, SR, VRt = np.linalg.svd(R)
+        U, sig = U @ VRt.T, SR
+    kk = min(p.k, U.shape[1])
+    U, sig = U[:, :kk], sig[:kk]
+    z = O.sign_reference(p.seed, m_global)[row0:row0 + U.shape[0]]
+    sgn = np.sign(allreduce(U.T @ z))
+    sgn[sgn == 0] = 1.0
+    return U * sgn, sig, draws, measures
