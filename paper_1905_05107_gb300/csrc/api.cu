@@ -131,6 +131,7 @@ struct pod_ctx {
     int32_t *r_rows, *r_rcnt, *r_h;
     void *Cbuf;
     void *Wbuf;      // W = Z M1 of the current round (m x cmax, ld m), from the QR2 pass
+    unsigned *sum_counter;   // arrival counter of the QR2 sums' G2 check
     // wide sizes: global scratch for the tall passes, the core, the first
     // CholeskyQR kernel and the refinement when their shared memory would not fit
     unsigned char *tall_gs, *core_gs, *chol_gs, *refine_gs, *ytall_gs;
@@ -174,7 +175,7 @@ static void ctx_free(pod_ctx *c) {
                     c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
-                    c->r_rcnt, c->r_h, c->Cbuf, c->Wbuf, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
+                    c->r_rcnt, c->r_h, c->Cbuf, c->Wbuf, c->sum_counter, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
                     c->tc_part, c->tc_counters, c->tall_gs, c->core_gs, c->chol_gs, c->refine_gs, c->ytall_gs};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -472,12 +473,35 @@ static pod_status enqueue_round(pod_ctx *c) {
     }
     ta.Wout = (T *)c->Wbuf;
     ta.ldw = c->p.m;
+    // the three passes leave their per-CTA partials to k_sum_parts, which
+    // spreads the fixed-order sums over many CTAs (one CTA summing all
+    // partials was 40% of a pass)
+    ta.defer = 1;
+    SumParts sp{};
+    sp.part = c->part;
+    sp.nparts = c->plan.grid;
+    sp.ld = c->cmax;
+    sp.rows_rect = c->rmax;
+    sp.st = c->st;
     ta.out = c->P;
     POD_TRY(launch_tall<T>(TALL_PROJ, ta, c->plan, s));
+    mark(c);
+    sp.stride = ta.part_stride;
+    sp.out = c->P;
+    sp.rect = 1;
+    sp.tri = 0;
+    POD_TRY(launch_sum_parts(sp, c->cmax, s));
     mark(c);
     ta.part_stride = sPG;
     ta.out = c->PG;
     POD_TRY(launch_tall<T>(TALL_CGS, ta, c->plan, s));
+    mark(c);
+    sp.stride = sPG;
+    sp.out = c->PG;
+    sp.rect = 1;
+    sp.tri = 1;
+    sp.tri_off = (int64_t)c->rmax * c->cmax;
+    POD_TRY(launch_sum_parts(sp, c->cmax, s));
     mark(c);
     SmallArgs sm = small_args(c);
     sm.tape = c->p.keep_tape ? c->tape_d : nullptr;
@@ -488,6 +512,16 @@ static pod_status enqueue_round(pod_ctx *c) {
     ta.out = c->G2;
     POD_TRY(launch_tall<T>(TALL_QR2, ta, c->plan, s));
     mark(c);
+    sp.stride = ta.part_stride;
+    sp.out = c->G2;
+    sp.rect = 0;
+    sp.tri = 1;
+    sp.tri_off = 0;
+    sp.check = c->st;
+    sp.counter = c->sum_counter;
+    POD_TRY(launch_sum_parts(sp, c->cmax, s));
+    mark(c);
+    ta.defer = 0;
     // when G2 is far from I (flagged by the QR2 pass itself) the residual
     // block was too ill-conditioned for an FP32 first Gram: redo CGS with a
     // compensated Gram, the Cholesky and QR2; otherwise these return at once
@@ -949,6 +983,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     unsigned char *Wb = nullptr;
     ALLOC(Wb, (size_t)m * cm * es);
     c->Wbuf = Wb;
+    ALLOC(c->sum_counter, 1);
     ALLOC(c->sigma, rm);
     ALLOC(c->s, n);
     ALLOC(c->ort, n);
@@ -1053,6 +1088,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_g, 0, (n + 1) * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, (64 + c->plan.groups) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->atu_counters, 0, (c->aplan.grid.x + 64) * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sum_counter, 0, sizeof(unsigned), s);
     if (p->rows) {
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_cnt, 0, (size_t)m * sizeof(unsigned), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_h, 0, sizeof(int32_t), s);

@@ -71,7 +71,27 @@ struct TallArgs {
                             // cond = 0 sets st->robust from its G2
     T *Wout;                // QR2 pass: W = (Z - U P2) M1 stored here (m x g, ld ldw),
     int64_t ldw;            // the block the UPDATE pass then combines (or null)
+    int defer;              // 1: write this CTA's partial and return; k_sum_parts sums
 };
+
+// Fixed-order sums of the tall passes' per-CTA FP64 partials, spread over
+// many CTAs (one row of outputs and 32 columns per CTA).  The used entries:
+// a rectangle (rows l < r_cur, columns j < g, at offset 0) and/or an upper
+// triangle (p <= q < g, at tri_off), both with leading dimension ld.
+struct SumParts {
+    const double *part;
+    int64_t stride;         // doubles per partial
+    int nparts;
+    double *out;
+    int ld;
+    int rect, tri;
+    int rows_rect;          // grid rows reserved for the rectangle (its capacity)
+    int64_t tri_off;
+    const DevState *st;
+    DevState *check;        // QR2: flag the round from |G2 - I| (or null)
+    unsigned *counter;      // arrival counter of the check, zero between launches
+};
+pod_status launch_sum_parts(const SumParts &a, int cols_cap, cudaStream_t s);
 
 enum TallKind { TALL_PROJ = 0, TALL_CGS = 1, TALL_QR2 = 2, TALL_UPDATE = 3 };
 

@@ -344,6 +344,104 @@ __host__ __device__ inline size_t gscratch_bytes(const SmemPlan &p) {
     return (((p.s1 + p.s2 + p.s3) * sizeof(T) + 15) / 16) * 16 + (p.acc1 + p.acc2) * 8;
 }
 
+// The second CholeskyQR Gram must be near I on its kept indices; if not, the
+// first pass lost accuracy (an ill-conditioned residual block): flag the
+// round for the compensated rerun (or'ed with the first Cholesky's drop
+// test).  Run by one whole CTA of TALL_THREADS threads on the final G2.
+__device__ void g2_check(const double *G2, int g, int cmax, DevState *st) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    double dev = 0.0;
+    for (int e = tid; e < g * g; e += bd) {
+        const int i = e / g, j = e - i * g;
+        if (i > j) continue;
+        const double gii = __ldcg(G2 + i * cmax + i), gjj = __ldcg(G2 + j * cmax + j);
+        if (gii == 0.0 || gjj == 0.0) continue;   // dropped index
+        const double d = fabs(__ldcg(G2 + i * cmax + j) - (i == j ? 1.0 : 0.0));
+        dev = (d != d) ? 1e300 : (d > dev ? d : dev);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_xor_sync(0xffffffffu, dev, o);
+        dev = y > dev ? y : dev;
+    }
+    __shared__ double wmax[TALL_THREADS / 32];
+    if ((tid & 31) == 0) wmax[tid >> 5] = dev;
+    __syncthreads();
+    if (tid == 0) {
+        double mx = 0.0;
+        for (int w = 0; w < (bd >> 5); ++w) mx = wmax[w] > mx ? wmax[w] : mx;
+        const int rb = st->robust || mx > 0.1;
+        st->robust = rb;
+        st->robust_rounds += rb;
+    }
+}
+
+// Sums of the deferred partials: CTA (x, y) owns output row y (rectangle
+// rows first, then triangle rows) and columns 32x .. 32x + 31; warp w adds
+// partials w, w + 8, w + 16, ... in that order (four loads in flight), and
+// the eight warp sums are added in warp order: a fixed order, so results
+// are reproducible run to run.  With a check, the last CTA to arrive
+// inspects the finished G2.
+constexpr int SUM_THREADS = 256;
+__global__ void __launch_bounds__(SUM_THREADS) k_sum_parts(SumParts a) {
+    const DevState *st = a.st;
+    if (st->done) return;
+    const int r = st->r_cur, g = st->g;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int row = blockIdx.y, c0 = 0;
+    int64_t off = 0;
+    bool act;
+    if (a.rect && row < a.rows_rect) {
+        act = row < r;
+        off = (int64_t)row * a.ld;
+    } else {
+        row -= a.rect ? a.rows_rect : 0;
+        act = a.tri && row < g;
+        off = a.tri_off + (int64_t)row * a.ld;
+        c0 = row;
+    }
+    const int j = blockIdx.x * 32 + lane;
+    const bool live = act && j >= c0 && j < g;
+    __shared__ double red[SUM_THREADS / 32][32];
+    if (act && blockIdx.x * 32 + 31 >= c0 && blockIdx.x * 32 < g) {
+        double s = 0.0;
+        if (live) {
+            const double *p0 = a.part + off + j;
+            int b = w;
+            for (; b + 24 < a.nparts; b += 32) {
+                const double v0 = __ldcg(p0 + (int64_t)b * a.stride), v1 = __ldcg(p0 + (int64_t)(b + 8) * a.stride);
+                const double v2 = __ldcg(p0 + (int64_t)(b + 16) * a.stride), v3 = __ldcg(p0 + (int64_t)(b + 24) * a.stride);
+                s += v0;
+                s += v1;
+                s += v2;
+                s += v3;
+            }
+            for (; b < a.nparts; b += 8) s += __ldcg(p0 + (int64_t)b * a.stride);
+        }
+        red[w][lane] = s;
+        __syncthreads();
+        if (w == 0 && live) {
+            double t = 0.0;
+            for (int k = 0; k < SUM_THREADS / 32; ++k) t += red[k][lane];
+            a.out[off + j] = t;
+        }
+    }
+    if (a.check) {
+        __shared__ int s_last;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned total = gridDim.x * gridDim.y;
+            s_last = atomicAdd(a.counter, 1u) == total - 1;
+            if (s_last) *a.counter = 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            g2_check(a.out + a.tri_off, g, a.ld, a.check);
+        }
+    }
+}
+
 template <typename T, int KIND>
 __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     const DevState *st = a.st;
@@ -548,36 +646,11 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
             if (p <= q) out[p * a.cmax + q] = acc_read<T>(&acc2[p * L.c4 + q]);
         }
     }
+    if (a.defer) return;   // summed by k_sum_parts
     const bool last = tall_reduce(a.part, a.gsum, a.out, (int)a.part_stride, a.part_stride, a.counters, s_flag);
     if (KIND == TALL_QR2 && !a.cond && last) {
-        // the second CholeskyQR Gram must be near I on its kept indices; if
-        // not, the first pass lost accuracy (an ill-conditioned residual
-        // block): flag the round for the compensated rerun
         __threadfence();
-        double dev = 0.0;
-        for (int e = tid; e < g * g; e += bd) {
-            const int i = e / g, j = e - i * g;
-            if (i > j) continue;
-            const double gii = __ldcg(a.out + i * a.cmax + i), gjj = __ldcg(a.out + j * a.cmax + j);
-            if (gii == 0.0 || gjj == 0.0) continue;   // dropped index
-            const double d = fabs(__ldcg(a.out + i * a.cmax + j) - (i == j ? 1.0 : 0.0));
-            dev = (d != d) ? 1e300 : (d > dev ? d : dev);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_xor_sync(0xffffffffu, dev, o);
-            dev = y > dev ? y : dev;
-        }
-        __shared__ double wmax[TALL_THREADS / 32];
-        if ((tid & 31) == 0) wmax[tid >> 5] = dev;
-        __syncthreads();
-        if (tid == 0) {
-            double mx = 0.0;
-            for (int w = 0; w < TALL_THREADS / 32; ++w) mx = wmax[w] > mx ? wmax[w] : mx;
-            DevState *sw = const_cast<DevState *>(st);
-            const int rb = sw->robust || mx > 0.1;   // or'ed with the Cholesky's drop test
-            sw->robust = rb;
-            sw->robust_rounds += rb;
-        }
+        g2_check(a.out, g, a.cmax, const_cast<DevState *>(st));
     }
 }
 
@@ -695,6 +768,15 @@ pod_status launch_kind(const TallArgs<T> &a, const TallPlan &plan, cudaStream_t 
 }
 
 }  // namespace
+
+pod_status launch_sum_parts(const SumParts &a, int cols_cap, cudaStream_t s) {
+    const int rows = (a.rect ? a.rows_rect : 0) + (a.tri ? cols_cap : 0);
+    dim3 grid((unsigned)((cols_cap + 31) / 32), (unsigned)rows);
+    k_sum_parts<<<grid, SUM_THREADS, 0, s>>>(a);
+    POD_CUDA_TRY(cudaGetLastError());
+    return POD_OK;
+}
+
 
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
     TallPlan p{};
