@@ -125,17 +125,36 @@ __device__ __forceinline__ double acc_read(const double *slot) {
 // outputs over 4-row chunks; tiles with ti > tj skipped when sym.  acc has
 // leading dimension ldacc (slots as in acc_add); red holds blockDim*16 T.
 // Ends with a barrier.
+// Tile t of the output grid: row-major over ta x tb tiles, or over the upper
+// triangle (ti <= tj) of a tb x tb grid when sym.
+__device__ __forceinline__ void tile_of(int t, int tb, bool sym, int &ti, int &tj) {
+    if (!sym) {
+        ti = t / tb;
+        tj = t - ti * tb;
+        return;
+    }
+    int i = 0, rem = t;
+    while (rem >= tb - i) {
+        rem -= tb - i;
+        ++i;
+    }
+    ti = i;
+    tj = i + rem;
+}
+
 template <typename T>
 __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm, bool sym, double *acc,
                          int ldacc, T *red) {
     const int tid = threadIdx.x, bd = blockDim.x;
-    const int ta = (na + 3) >> 2, tb = (nb + 3) >> 2, nT = ta * tb;
+    const int ta = (na + 3) >> 2, tb = (nb + 3) >> 2;
+    // only the tiles that are computed (the upper triangle when sym) share out the threads
+    const int nT = sym ? tb * (tb + 1) / 2 : ta * tb;
     const int chunks = bm >> 2;
     if (nT == 0) return;
     if (nT * 2 > bd) {
         for (int tile = tid; tile < nT; tile += bd) {
-            const int ti = tile / tb, tj = tile - ti * tb;
-            if (sym && ti > tj) continue;
+            int ti, tj;
+            tile_of(tile, tb, sym, ti, tj);
             T a[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) a[e] = (T)0;
@@ -162,11 +181,12 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
     }
     const int RG = bd / nT;
     const int tile = tid % nT, grp = tid / nT;
-    const int ti = tile / tb, tj = tile - ti * tb;
+    int ti, tj;
+    tile_of(tile, tb, sym, ti, tj);
     T a[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) a[e] = (T)0;
-    if (grp < RG && !(sym && ti > tj)) {
+    if (grp < RG) {
         for (int rc = grp; rc < chunks; rc += RG) {
             T x[4][4], y[4][4];
 #pragma unroll
@@ -180,16 +200,14 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 #pragma unroll
                     for (int w = 0; w < 4; ++w) a[u * 4 + v] = fma(x[u][w], y[v][w], a[u * 4 + v]);
         }
-    }
-    if (grp < RG) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) red[(grp * nT + tile) * 16 + e] = a[e];
     }
     __syncthreads();
     for (int e = tid; e < nT * 16; e += bd) {
         const int t2 = e >> 4, uv = e & 15;
-        const int i2 = t2 / tb, j2 = t2 - i2 * tb;
-        if (sym && i2 > j2) continue;
+        int i2, j2;
+        tile_of(t2, tb, sym, i2, j2);
         T s = (T)0;
         for (int g2 = 0; g2 < RG; ++g2) s += red[(g2 * nT + t2) * 16 + uv];
         acc_add(&acc[(4 * i2 + (uv >> 2)) * ldacc + 4 * j2 + (uv & 3)], s);
