@@ -542,13 +542,30 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_small_chol(SmallArgs a) {
     const double *P2 = a.PG;
     const double *G = a.PG + (int64_t)a.rmax * a.cmax;
 
+    // Ptot over all (l, j) at once (the global loads spread over the CTA),
+    // then the squared column norms of the block from the squares in Mw
+    // (Mw holds ld^2 8-byte entries; with r g beyond that, per column)
+    double *sq = reinterpret_cast<double *>(Mw);
+    const bool spread = r * g <= ld * ld;
+    if (spread)
+        for (int e = tid; e < r * g; e += bd) {
+            const int l = e / g, j = e - l * g;
+            const double pt = round_to(a.dtype, a.P[l * ld + j]) + round_to(a.dtype, P2[l * ld + j]);
+            a.Ptot[l * ld + j] = pt;
+            sq[e] = pt * pt;
+        }
+    __syncthreads();
     double cmax2 = 0.0;
     for (int j = tid; j < g; j += bd) {
         double cn = G[j * ld + j];
         for (int l = 0; l < r; ++l) {
-            double pt = round_to(a.dtype, a.P[l * ld + j]) + round_to(a.dtype, P2[l * ld + j]);
-            a.Ptot[l * ld + j] = pt;
-            cn += pt * pt;
+            if (spread) {
+                cn += sq[l * g + j];
+            } else {
+                const double pt = round_to(a.dtype, a.P[l * ld + j]) + round_to(a.dtype, P2[l * ld + j]);
+                a.Ptot[l * ld + j] = pt;
+                cn += pt * pt;
+            }
         }
         cmax2 = cn > cmax2 ? cn : cmax2;
     }
@@ -994,11 +1011,15 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         // error of direction j by sigma_j / sigma_s).  Vr_s = E b_s in
         // double-float, orthonormalised by CholeskyQR (leading spans kept);
         // then sigma_s = |E^T q_s| (Rayleigh quotient).
+        // E is upper triangular (diag(Sigma) and P in its first r rows, R in
+        // the rest): row p < r holds sigma_p at column p and P at columns >= r,
+        // row p >= r holds R at columns >= p
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
             const J *bs = B + (size_t)order[s] * ldj;
             X acc = XOps<X>::zero();
-            for (int j = 0; j < nc; ++j) acc = acc + Ex[j * nc + p] * XOps<X>::from_f((float)bs[j]);
+            if (p < r) acc = Ex[p * nc + p] * XOps<X>::from_f((float)bs[p]);
+            for (int j = p < r ? r : p; j < nc; ++j) acc = acc + Ex[j * nc + p] * XOps<X>::from_f((float)bs[j]);
             Vr[s * nc + p] = acc;
         }
         __syncthreads();
@@ -1128,8 +1149,13 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         __syncthreads();
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, j = e % nc;
+            // column j of E: sigma_j alone for j < r, rows 0..j otherwise
             X acc = XOps<X>::zero();
-            for (int p = 0; p < nc; ++p) acc = acc + Ex[j * nc + p] * Q[s * nc + p];
+            if (j < r) {
+                acc = Ex[j * nc + j] * Q[s * nc + j];
+            } else {
+                for (int p = 0; p <= j; ++p) acc = acc + Ex[j * nc + p] * Q[s * nc + p];
+            }
             Yt[s * nc + j] = acc;
         }
         __syncthreads();
