@@ -132,6 +132,7 @@ struct pod_ctx {
     void *Cbuf;
     void *Wbuf;      // W = Z M1 of the current round (m x cmax, ld m), from the QR2 pass
     unsigned *sum_counter;   // arrival counter of the QR2 sums' G2 check
+    unsigned *upd_counter;   // arrival counter of the UPDATE pass (end of the round)
     // wide sizes: global scratch for the tall passes, the core, the first
     // CholeskyQR kernel and the refinement when their shared memory would not fit
     unsigned char *tall_gs, *core_gs, *chol_gs, *refine_gs, *ytall_gs;
@@ -175,7 +176,7 @@ static void ctx_free(pod_ctx *c) {
                     c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
-                    c->r_rcnt, c->r_h, c->Cbuf, c->Wbuf, c->sum_counter, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
+                    c->r_rcnt, c->r_h, c->Cbuf, c->Wbuf, c->sum_counter, c->upd_counter, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
                     c->tc_part, c->tc_counters, c->tall_gs, c->core_gs, c->chol_gs, c->refine_gs, c->ytall_gs};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -551,11 +552,10 @@ static pod_status enqueue_round(pod_ctx *c) {
         ua.lda = c->p.m;
         ua.Wout = nullptr;
         ua.vec = (c->p.m * (int64_t)sizeof(T)) % 16 == 0;
+        ua.finish = c->upd_counter;   // its last CTA also ends the round
         POD_TRY(launch_tall<T>(TALL_UPDATE, ua, c->plan, s));
         mark(c);
     }
-    POD_TRY(launch_finish(c->st, s));
-    mark(c);
     return POD_OK;
 }
 
@@ -984,6 +984,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     ALLOC(Wb, (size_t)m * cm * es);
     c->Wbuf = Wb;
     ALLOC(c->sum_counter, 1);
+    ALLOC(c->upd_counter, 1);
     ALLOC(c->sigma, rm);
     ALLOC(c->s, n);
     ALLOC(c->ort, n);
@@ -1089,6 +1090,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, (64 + c->plan.groups) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->atu_counters, 0, (c->aplan.grid.x + 64) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sum_counter, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->upd_counter, 0, sizeof(unsigned), s);
     if (p->rows) {
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_cnt, 0, (size_t)m * sizeof(unsigned), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_h, 0, sizeof(int32_t), s);

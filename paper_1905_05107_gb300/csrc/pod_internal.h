@@ -72,6 +72,8 @@ struct TallArgs {
     T *Wout;                // QR2 pass: W = (Z - U P2) M1 stored here (m x g, ld ldw),
     int64_t ldw;            // the block the UPDATE pass then combines (or null)
     int defer;              // 1: write this CTA's partial and return; k_sum_parts sums
+    unsigned *finish;       // UPDATE of a round: arrival counter; the last CTA ends the
+                            // round (r_cur <- r_new, t + 1, the stop decision), or null
 };
 
 // Fixed-order sums of the tall passes' per-CTA FP64 partials, spread over
@@ -355,7 +357,6 @@ pod_status launch_core(const SmallArgs &a, cudaStream_t s);
 size_t core_smem_bytes(int rmax, int cmax, int dtype);
 size_t core_jacobi_bytes(int rmax, int cmax, int dtype);   // shared memory of the Jacobi arrays alone
 size_t small_chol_smem(int cmax);
-pod_status launch_finish(DevState *st, cudaStream_t s);
 
 
 // refinement QR(A^T U), SVD(R)

@@ -271,30 +271,29 @@ __device__ int jacobi_hw(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *al
 
 // Lean FP32 variant for n_c <= 64, same ordering, thresholds and stopping
 // rule as jacobi_lp.  B (and V) have leading dimension 64 with zero rows
-// beyond nrow, so LP lanes hold a column pair as 64 / LP rows per lane with
-// no bounds tests; the pairs of a warp visit their rows in rotated order so
-// that their shared-memory accesses fall in disjoint banks; each lane group
-// keeps its pair indices in registers and advances them by one per round;
-// the rotation uses the fast reciprocal and reciprocal square root (an FP32
-// rotation orthogonal to a few ulp is all the double-float finish needs).
-// V is rotated only when WITHV.
+// beyond nrow, so four lanes hold a column pair as four 16-byte row groups
+// each, with no bounds tests; the pairs of a warp take their row groups in
+// rotated order so that each 8-lane phase of a 16-byte access touches all 32
+// banks once; each lane group keeps its pair indices in registers and
+// advances them by one per round; the rotation uses reciprocal square roots
+// only (an FP32 rotation orthogonal to a few ulp is all the double-float
+// finish needs).  V is rotated only when WITHV.  (Four lanes per pair
+// measured faster than 8 or 16 on 60-column cores, and 16-byte row groups
+// than 4-byte rows.)
 constexpr int LEAN_LD = 64;
-// lanes per column pair: four (16 rows per lane, 8 pairs per warp) measured
-// fastest of 4, 8 and 16 on the 60-column cores
-constexpr int JLP = 4;
 
-template <int LP, bool WITHV>
+template <bool WITHV>
 __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol, int max_sweeps, int *s_flag) {
-    constexpr int E = LEAN_LD / LP, PPW = 32 / LP;
+    constexpr int LP = 4, PPW = 8;
     const int N = ncol + (ncol & 1), npairs = N / 2, M = N - 1;
     const int nwork = 32 * ((npairs + PPW - 1) / PPW);
     const int tid = threadIdx.x;
     if (tid >= nwork) return 0;
     const int lane = tid & 31, lp = lane % LP, sub = lane / LP, pr = (tid >> 5) * PPW + sub;
     const bool active = pr < npairs;
-    int rows[E];
+    int off[4];   // float4 index of row group k: rows 16 ((k + sub) mod 4) + 4 lp .. + 3
 #pragma unroll
-    for (int e = 0; e < E; ++e) rows[e] = lp + LP * ((e + sub) % E);
+    for (int k = 0; k < 4; ++k) off[k] = 4 * ((k + sub) & 3) + lp;
     const float tol2 = tol * tol, loose = 16.f * tol, loose2 = loose * loose;
     int sweep = 0;
     for (;; ++sweep) {
@@ -317,23 +316,26 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
         for (int rnd = 0; rnd < M; ++rnd) {
             const int p = active ? min(pa, qa) : 0, q = active ? max(pa, qa) : 0;
             const bool valid = active && q < ncol;
-            float *bp = B + (size_t)p * LEAN_LD, *bq = B + (size_t)(valid ? q : p) * LEAN_LD;
-            float x[E], y[E];
+            float4 *bp = reinterpret_cast<float4 *>(B + (size_t)p * LEAN_LD);
+            float4 *bq = reinterpret_cast<float4 *>(B + (size_t)(valid ? q : p) * LEAN_LD);
+            float4 x[4], y[4];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                x[e] = bp[rows[e]];
-                y[e] = bq[rows[e]];
+            for (int k = 0; k < 4; ++k) {
+                x[k] = bp[off[k]];
+                y[k] = bq[off[k]];
             }
             const float a = alpha[p], b = alpha[valid ? q : p];
             float g0 = 0.f, g1 = 0.f;
 #pragma unroll
-            for (int e = 0; e < E; e += 2) {
-                g0 = fmaf(x[e], y[e], g0);
-                g1 = fmaf(x[e + 1], y[e + 1], g1);
+            for (int k = 0; k < 4; ++k) {
+                g0 = fmaf(x[k].x, y[k].x, g0);
+                g1 = fmaf(x[k].y, y[k].y, g1);
+                g0 = fmaf(x[k].z, y[k].z, g0);
+                g1 = fmaf(x[k].w, y[k].w, g1);
             }
             float g = g0 + g1;
-#pragma unroll
-            for (int o = LP / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, LP);
+            g += __shfl_xor_sync(0xffffffffu, g, 2, LP);
+            g += __shfl_xor_sync(0xffffffffu, g, 1, LP);
             if (valid) {
                 const float ab = a * b, g2 = g * g;
                 if (ab > 0.f && g2 > loose2 * ab && lp == 0) s_flag[1] = 1;
@@ -350,17 +352,22 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
                     const float sn = copysignf(1.f, d) * (0.5f * h) * (ir * iy);
                     const float t = sn * iy;
 #pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        bp[rows[e]] = fmaf(cs, x[e], -sn * y[e]);
-                        bq[rows[e]] = fmaf(sn, x[e], cs * y[e]);
+                    for (int k = 0; k < 4; ++k) {
+                        bp[off[k]] = make_float4(fmaf(cs, x[k].x, -sn * y[k].x), fmaf(cs, x[k].y, -sn * y[k].y),
+                                                 fmaf(cs, x[k].z, -sn * y[k].z), fmaf(cs, x[k].w, -sn * y[k].w));
+                        bq[off[k]] = make_float4(fmaf(sn, x[k].x, cs * y[k].x), fmaf(sn, x[k].y, cs * y[k].y),
+                                                 fmaf(sn, x[k].z, cs * y[k].z), fmaf(sn, x[k].w, cs * y[k].w));
                     }
                     if (WITHV) {
-                        float *vp = V + (size_t)p * LEAN_LD, *vq = V + (size_t)q * LEAN_LD;
+                        float4 *vp = reinterpret_cast<float4 *>(V + (size_t)p * LEAN_LD);
+                        float4 *vq = reinterpret_cast<float4 *>(V + (size_t)q * LEAN_LD);
 #pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            const float vx = vp[rows[e]], vy = vq[rows[e]];
-                            vp[rows[e]] = fmaf(cs, vx, -sn * vy);
-                            vq[rows[e]] = fmaf(sn, vx, cs * vy);
+                        for (int k = 0; k < 4; ++k) {
+                            const float4 vx = vp[off[k]], vy = vq[off[k]];
+                            vp[off[k]] = make_float4(fmaf(cs, vx.x, -sn * vy.x), fmaf(cs, vx.y, -sn * vy.y),
+                                                     fmaf(cs, vx.z, -sn * vy.z), fmaf(cs, vx.w, -sn * vy.w));
+                            vq[off[k]] = make_float4(fmaf(sn, vx.x, cs * vy.x), fmaf(sn, vx.y, cs * vy.y),
+                                                     fmaf(sn, vx.z, cs * vy.z), fmaf(sn, vx.w, cs * vy.w));
                         }
                     }
                     if (lp == 0) {
@@ -993,8 +1000,8 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     if (tid == 0) s_flag[1] = 0;
     int nsweeps;
     if constexpr (sizeof(J) == 4) {
-        if (lean && a.tape) nsweeps = jacobi_lean<JLP, true>(B, nc, V, alpha, tol, 20, s_flag);
-        else if (lean) nsweeps = jacobi_lean<JLP, false>(B, nc, V, alpha, tol, 20, s_flag);
+        if (lean && a.tape) nsweeps = jacobi_lean<true>(B, nc, V, alpha, tol, 20, s_flag);
+        else if (lean) nsweeps = jacobi_lean<false>(B, nc, V, alpha, tol, 20, s_flag);
         else nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 20, s_flag);
     } else {
         nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 30, s_flag);
@@ -1327,22 +1334,6 @@ pod_status launch_core(const SmallArgs &a, cudaStream_t s) {
     return POD_OK;
 }
 
-// ---------------------------------------------------------------------------
-// End of a round: r_cur <- r_new, t <- t + 1, apply the stop decision.
-// ---------------------------------------------------------------------------
-__global__ void k_finish(DevState *st) {
-    if (threadIdx.x != 0 || st->done) return;
-    st->r_cur = st->r_new;
-    st->t += 1;
-    st->rounds_run += 1;
-    if (st->done_next) st->done = 1;
-}
-
-pod_status launch_finish(DevState *st, cudaStream_t s) {
-    k_finish<<<1, 32, 0, s>>>(st);
-    POD_CUDA_TRY(cudaGetLastError());
-    return POD_OK;
-}
 
 // ---------------------------------------------------------------------------
 // Refinement (closing lines of Algorithm 1): with Y = A^T U (n x r),

@@ -639,7 +639,23 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         __syncthreads();
     }
     cp_async_wait<0>();
-    if (KIND == TALL_UPDATE) return;
+    if (KIND == TALL_UPDATE) {
+        if (a.finish) {
+            // end of the round, by the last CTA to finish its rows (every CTA
+            // read the round's sizes before arriving)
+            __threadfence();
+            __syncthreads();
+            if (tid == 0 && atomicAdd(a.finish, 1u) == gridDim.x - 1) {
+                *a.finish = 0;
+                DevState *sw = const_cast<DevState *>(st);
+                sw->r_cur = sw->r_new;
+                sw->t += 1;
+                sw->rounds_run += 1;
+                if (sw->done_next) sw->done = 1;
+            }
+        }
+        return;
+    }
     // this CTA's FP64 partial, then the in-kernel fixed-order sum
     double *out = a.part + (int64_t)blockIdx.x * a.part_stride;
     if (KIND == TALL_PROJ) {

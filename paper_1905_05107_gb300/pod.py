@@ -33,7 +33,7 @@ EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay
             "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental", "pod_robust_rounds"]
 
 ROUND_KERNELS = ["sample", "proj", "proj_sum", "cgs_gram", "cgs_sum", "chol1", "qr2_gram", "qr2_sum", "cgs_robust",
-                 "chol1_robust", "qr2_robust", "core_svd", "update", "finish"]
+                 "chol1_robust", "qr2_robust", "core_svd", "update"]
 ORT_KERNELS = ["ort_atu", "ort_values"]
 ROW_KERNELS = ["rows_sample", "rows_gram", "rows_chol", "rows_core", "rows_block", "rows_setg"]
 
