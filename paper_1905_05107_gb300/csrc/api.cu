@@ -133,6 +133,7 @@ struct pod_ctx {
     void *Wbuf;      // W = Z M1 of the current round (m x cmax, ld m), from the QR2 pass
     unsigned *sum_counter;   // arrival counter of the QR2 sums' G2 check
     unsigned *upd_counter;   // arrival counter of the UPDATE pass (end of the round)
+    unsigned long long *g2dev;   // running max |G2 - I| of the QR2 sums
     // wide sizes: global scratch for the tall passes, the core, the first
     // CholeskyQR kernel and the refinement when their shared memory would not fit
     unsigned char *tall_gs, *core_gs, *chol_gs, *refine_gs, *ytall_gs;
@@ -176,7 +177,7 @@ static void ctx_free(pod_ctx *c) {
                     c->replay_idx, c->replay_off, c->gsum, c->counters, c->atu_counters,
                     c->r_val, c->r_bmax, c->r_rscale, c->GW, c->rYm, c->part_w, c->gsum_w, c->r_bsum,
                     c->r_boff, c->r_total, c->r_w, c->r_cdf, c->r_cnt, c->counters_w, c->r_rows,
-                    c->r_rcnt, c->r_h, c->Cbuf, c->Wbuf, c->sum_counter, c->upd_counter, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
+                    c->r_rcnt, c->r_h, c->Cbuf, c->Wbuf, c->sum_counter, c->upd_counter, c->g2dev, c->wR1p, c->wG2, c->wM1, c->wsig, c->wX,
                     c->tc_part, c->tc_counters, c->tall_gs, c->core_gs, c->chol_gs, c->refine_gs, c->ytall_gs};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -520,6 +521,7 @@ static pod_status enqueue_round(pod_ctx *c) {
     sp.tri_off = 0;
     sp.check = c->st;
     sp.counter = c->sum_counter;
+    sp.devmax = c->g2dev;
     POD_TRY(launch_sum_parts(sp, c->cmax, s));
     mark(c);
     ta.defer = 0;
@@ -985,6 +987,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     c->Wbuf = Wb;
     ALLOC(c->sum_counter, 1);
     ALLOC(c->upd_counter, 1);
+    ALLOC(c->g2dev, 1);
     ALLOC(c->sigma, rm);
     ALLOC(c->s, n);
     ALLOC(c->ort, n);
@@ -1091,6 +1094,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (e == cudaSuccess) e = cudaMemsetAsync(c->atu_counters, 0, (c->aplan.grid.x + 64) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sum_counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->upd_counter, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->g2dev, 0, sizeof(unsigned long long), s);
     if (p->rows) {
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_cnt, 0, (size_t)m * sizeof(unsigned), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->r_h, 0, sizeof(int32_t), s);

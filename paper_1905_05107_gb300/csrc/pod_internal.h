@@ -92,6 +92,7 @@ struct SumParts {
     const DevState *st;
     DevState *check;        // QR2: flag the round from |G2 - I| (or null)
     unsigned *counter;      // arrival counter of the check, zero between launches
+    unsigned long long *devmax;   // running max |G2 - I| (bits of a double >= 0), zero between launches
 };
 pod_status launch_sum_parts(const SumParts &a, int cols_cap, cudaStream_t s);
 

@@ -437,10 +437,23 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sum_parts(SumParts a) {
         }
         red[w][lane] = s;
         __syncthreads();
-        if (w == 0 && live) {
-            double t = 0.0;
-            for (int k = 0; k < SUM_THREADS / 32; ++k) t += red[k][lane];
-            a.out[off + j] = t;
+        if (w == 0) {
+            double dev = 0.0;
+            if (live) {
+                double t = 0.0;
+                for (int k = 0; k < SUM_THREADS / 32; ++k) t += red[k][lane];
+                a.out[off + j] = t;
+                // |G2 - I| on the kept indices: a dropped index has a zero row,
+                // column and diagonal
+                if (a.check) {
+                    const double d = j == row ? (t == 0.0 ? 0.0 : fabs(t - 1.0)) : fabs(t);
+                    dev = d != d ? 1e300 : d;
+                }
+            }
+            if (a.check) {
+                for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+                if (lane == 0 && dev > 0.0) atomicMax(a.devmax, (unsigned long long)__double_as_longlong(dev));
+            }
         }
     }
     if (a.check) {
@@ -449,13 +462,16 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sum_parts(SumParts a) {
         __syncthreads();
         if (tid == 0) {
             const unsigned total = gridDim.x * gridDim.y;
-            s_last = atomicAdd(a.counter, 1u) == total - 1;
-            if (s_last) *a.counter = 0;
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            g2_check(a.out + a.tri_off, g, a.ld, a.check);
+            if (atomicAdd(a.counter, 1u) == total - 1) {
+                // the last CTA: every row's deviation is in
+                __threadfence();
+                *a.counter = 0;
+                const double mx = __longlong_as_double((long long)atomicExch(a.devmax, 0ull));
+                DevState *sw = a.check;
+                const int rb = sw->robust || mx > 0.1;   // or'ed with the first Cholesky's drop test
+                sw->robust = rb;
+                sw->robust_rounds += rb;
+            }
         }
     }
 }
