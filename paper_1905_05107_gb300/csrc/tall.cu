@@ -15,11 +15,14 @@
 // used.  Every product is a 4x4 register tile fed by 128-bit shared loads:
 // the row-space products (C - U P, Z M1, U X + W Y) tile 4 rows x 4 output
 // columns, the Gram-type products (U^T C, Z^T Z) tile 4 x 4 outputs over
-// 4-row chunks.  FP32 tile sums are flushed into FP64 accumulators after
-// every slab.  The CTAs' FP64 partials are summed inside the kernel: the
-// last CTA to finish in each group of 16 sums its group, the last group sums
-// the groups, both in a fixed order (bit-reproducible), using atomic arrival
-// counters only (no waiting).
+// 4-row chunks.  FP32 tile sums are added into running sums after every
+// slab (double-float slots for FP32 data, FP64 for FP64 data).  Each CTA
+// writes its FP64 partial; in a round's PROJ, CGS and QR2 passes those are
+// summed by k_sum_parts (many CTAs, fixed order), elsewhere inside the kernel:
+// the last CTA to finish in each group of 16 sums its group, the last group
+// sums the groups, in a fixed order, using atomic arrival counters only (no
+// waiting).  Either way the sums are bit-reproducible.  The UPDATE pass of a
+// round also ends the round in its last CTA.
 #include "pod_internal.h"
 
 namespace {
