@@ -283,7 +283,16 @@ __device__ int jacobi_hw(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *al
 constexpr int LEAN_LD = 64;
 
 template <bool WITHV>
-__device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol, int max_sweeps, int *s_flag) {
+__device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol, int max_sweeps, int *s_flag,
+                           int keep_top = 0) {
+    // keep_top > 0: only the keep_top rows of largest norm are used afterwards,
+    // so from the third sweep on a pair whose squared norms are both below an
+    // eighth of the keep_top-th largest counts as converged (the rows among
+    // the rest need not be orthogonal to one another; every pair touching a
+    // leading row still is).  A Gershgorin test at the end confirms that the
+    // trailing rows hide no direction above the leading ones, else the sweeps
+    // go on over every pair.
+    __shared__ float s_thr;
     constexpr int LP = 4, PPW = 8;
     const int N = ncol + (ncol & 1), npairs = N / 2, M = N - 1;
     const int nwork = 32 * ((npairs + PPW - 1) / PPW);
@@ -296,6 +305,7 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
     for (int k = 0; k < 4; ++k) off[k] = 4 * ((k + sub) & 3) + lp;
     const float tol2 = tol * tol, loose = 16.f * tol, loose2 = loose * loose;
     int sweep = 0;
+    for (;;) {   // a second pass only when the guard below turns the skipping off
     for (;; ++sweep) {
         for (int c = tid; c < ncol; c += nwork) {
             const float4 *bc = reinterpret_cast<const float4 *>(B + (size_t)c * LEAN_LD);
@@ -311,6 +321,22 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
         if (tid == 0) s_flag[0] = 0;
         bar_sync_1(nwork);
         if (sweep >= max_sweeps || ncol < 2) break;
+        if (keep_top > 0 && keep_top < ncol) {
+            if (tid < 32) {
+                // the keep_top-th largest squared norm (ranks with ties by index)
+                for (int c = tid; c < ncol; c += 32) {
+                    const float ac = alpha[c];
+                    int rank = 0;
+                    for (int j = 0; j < ncol; ++j) {
+                        const float aj = alpha[j];
+                        rank += (aj > ac || (aj == ac && j < c)) ? 1 : 0;
+                    }
+                    if (rank == keep_top - 1) s_thr = sweep >= 2 ? 0.125f * ac : 0.f;
+                }
+            }
+            bar_sync_1(nwork);
+        }
+        const float thr = (keep_top > 0 && keep_top < ncol) ? s_thr : 0.f;
         // round 0 of the tournament: pair 0 = (M, 0), pair k = (k, M - k)
         int pa = pr == 0 ? M : pr, qa = pr == 0 ? 0 : M - pr;
         for (int rnd = 0; rnd < M; ++rnd) {
@@ -336,7 +362,7 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
             float g = g0 + g1;
             g += __shfl_xor_sync(0xffffffffu, g, 2, LP);
             g += __shfl_xor_sync(0xffffffffu, g, 1, LP);
-            if (valid) {
+            if (valid && (a >= thr || b >= thr)) {
                 const float ab = a * b, g2 = g * g;
                 if (ab > 0.f && g2 > loose2 * ab && lp == 0) s_flag[1] = 1;
                 if (ab > 0.f && g2 > tol2 * ab) {
@@ -399,6 +425,64 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
             }
             break;
         }
+    }
+    // guard: the trailing rows, not orthogonalised among themselves, must
+    // not hold a direction above the keep_top-th leading row.  Gershgorin:
+    // every eigenvalue of their Gram lies below max_i (alpha_i + sum_j
+    // |b_i . b_j|); if that reaches the keep_top-th largest alpha, the
+    // sweeps go on over every pair
+    if (keep_top > 0 && keep_top < ncol) {
+        __shared__ int s_top[LEAN_LD];
+        __shared__ float s_amin;
+        __shared__ int s_bad;
+        bar_sync_1(nwork);   // the final norms are in
+        if (tid == 0) s_bad = 0;
+        for (int c = tid; c < ncol; c += nwork) {
+            const float ac = alpha[c];
+            int rank = 0;
+            for (int j = 0; j < ncol; ++j) {
+                const float aj = alpha[j];
+                rank += (aj > ac || (aj == ac && j < c)) ? 1 : 0;
+            }
+            s_top[c] = rank < keep_top;
+            if (rank == keep_top - 1) s_amin = ac;
+        }
+        bar_sync_1(nwork);
+        // |b_i . b_j| of the trailing pairs into Dm (V's storage, unused
+        // without WITHV), spread over the threads; then each trailing row's
+        // radius in a fixed order
+        float *Dm = V;
+        for (int e = tid; e < ncol * ncol; e += nwork) {
+            const int i = e / ncol, j = e - i * ncol;
+            if (i >= j || s_top[i] || s_top[j]) continue;
+            const float4 *bi = reinterpret_cast<const float4 *>(B + (size_t)i * LEAN_LD);
+            const float4 *bj = reinterpret_cast<const float4 *>(B + (size_t)j * LEAN_LD);
+            float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < LEAN_LD / 4; k += 2) {
+                const float4 x0 = bi[k], y0 = bj[k], x1 = bi[k + 1], y1 = bj[k + 1];
+                d0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, fmaf(x0.z, y0.z, fmaf(x0.w, y0.w, d0))));
+                d1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, fmaf(x1.z, y1.z, fmaf(x1.w, y1.w, d1))));
+            }
+            const float d = fabsf(d0 + d1);
+            Dm[i * LEAN_LD + j] = d;
+            Dm[j * LEAN_LD + i] = d;
+        }
+        bar_sync_1(nwork);
+        for (int i = tid; i < ncol; i += nwork) {
+            if (s_top[i]) continue;
+            float rad = 0.f;
+            for (int j = 0; j < ncol; ++j)
+                if (j != i && !s_top[j]) rad += Dm[i * LEAN_LD + j];
+            if (alpha[i] + rad >= s_amin) s_bad = 1;
+        }
+        bar_sync_1(nwork);
+        if (s_bad && sweep < max_sweeps) {
+            keep_top = 0;
+            continue;
+        }
+    }
+    break;
     }
     return sweep;
 }
@@ -1001,7 +1085,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     int nsweeps;
     if constexpr (sizeof(J) == 4) {
         if (lean && a.tape) nsweeps = jacobi_lean<true>(B, nc, V, alpha, tol, 20, s_flag);
-        else if (lean) nsweeps = jacobi_lean<false>(B, nc, V, alpha, tol, 20, s_flag);
+        else if (lean) nsweeps = jacobi_lean<false>(B, nc, V, alpha, tol, 20, s_flag, a.wq ? (a.r < nc ? a.r : nc) : 0);
         else nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 20, s_flag);
     } else {
         nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 30, s_flag);

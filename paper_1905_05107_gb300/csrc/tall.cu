@@ -460,7 +460,6 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sum_parts(SumParts a) {
         }
     }
     if (a.check) {
-        __shared__ int s_last;
         __threadfence();
         __syncthreads();
         if (tid == 0) {
