@@ -19,8 +19,10 @@
  *    stream).  Work is ordered on that stream; only calls documented as
  *    synchronising wait for the device.
  *  - Every entry point returns a pod_status and never aborts the process.
- *    After POD_ECUDA or POD_ETIMEOUT from a context call the context is
- *    poisoned: only pod_destroy is valid on it.
+ *    After POD_ECUDA, POD_ETIMEOUT, POD_ENAN or POD_ERANK from a context
+ *    call the context is poisoned: pod_destroy and the host-only queries
+ *    (pod_counters, pod_row_draws) stay valid, every other call returns
+ *    POD_ESTATE.
  */
 #ifndef POD_GB300_H
 #define POD_GB300_H
@@ -283,6 +285,23 @@ POD_API pod_status pod_counters(pod_ctx *ctx, int64_t *kernel_launches, int32_t 
  */
 POD_API pod_status pod_core_stats(pod_ctx *ctx, int32_t *sweeps, int64_t *cycles);
 
+/*
+ * pod_set_wait_limit -- bound, in polls, of each pipeline wait (on an
+ * mbarrier) in this context's tensor-core kernels before the kernel gives up
+ * with POD_ETIMEOUT; 0 restores the default of 2^24 polls, far above any
+ * wait that can complete.  A small bound makes the waits run out on purpose,
+ * so that a caller can check that a kernel gives up cleanly: it records
+ * POD_ETIMEOUT, stops issuing work, lets its own copies and tensor-core
+ * operations in flight complete (those waits keep the default bound), frees
+ * its tensor memory and returns; the call that ran it returns POD_ETIMEOUT
+ * and poisons the context.  Applies to launches enqueued after the call
+ * (the round graph is captured at the first pod_iterate and keeps the bound
+ * it was captured with).  Host only, no GPU work.  The paper has no
+ * counterpart: it is a testing aid for the bounded-wait design.
+ * Errors: POD_EINVAL (NULL ctx), POD_ESTATE (poisoned context).
+ */
+POD_API pod_status pod_set_wait_limit(pod_ctx *ctx, uint32_t polls);
+
 /* pod_destroy -- free every workspace of ctx (NULL is a no-op). Synchronises. */
 POD_API void pod_destroy(pod_ctx *ctx);
 
@@ -376,18 +395,22 @@ POD_API pod_status pod_block_merge(int32_t dtype, int64_t m, const void *U1_dev,
 /*
  * pod_sample_noalloc -- the same draw step as pod_sample (same inputs, same
  * outputs, bit-identical results), for callers that cannot allocate device
- * memory: host or stream callbacks (where CUDA API calls that may allocate
- * are not allowed), processes whose device memory pool is capped or fully
- * reserved by another framework, and latency-critical loops that must not
- * touch the allocator.  It makes no allocation of any kind: its scratch
- * lives in fixed arrays compiled into the library, which every GPU that
- * loads the library holds (about 1.1 MB) until the process exits.
- * The paper has no counterpart to this entry point.
+ * memory when they draw: processes whose device memory pool is capped or
+ * fully reserved by another framework, and latency-critical loops that must
+ * not touch the allocator.  It allocates nothing: its scratch lives in fixed
+ * arrays compiled into the library, which every GPU that loads the library
+ * holds (about 1.1 MB) until the process exits.  It does make CUDA API calls
+ * (an address lookup, two copies, a launch), so it must not be called from
+ * a host callback (cudaLaunchHostFunc, cudaStreamAddCallback), where CUDA
+ * forbids them.  The paper has no counterpart to this entry point.
  *   Limits: n <= 65536 columns and c <= 4096 draws; larger sizes return
  *   POD_EUNSUPPORTED without doing anything.
  *   The first call on each device looks up the arrays' device addresses
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   outside any stream capture.
+ *   (cudaGetSymbolAddress) with that device current; under CUDA's lazy
+ *   module loading that lookup is also when the arrays are placed in device
+ *   memory, so it can fail with POD_ECUDA where nothing may be allocated.
+ *   Make one call per device at set-up, outside any stream capture and
+ *   while allocation is still possible.
  *   All calls share the arrays: calls that overlap on the GPU (different
  *   streams or host threads on one device) race and must be serialised by
  *   the caller.  Each call re-initialises the parts it needs.

@@ -307,6 +307,7 @@ class IterRecord:
     sigma: np.ndarray
     rows: Optional[np.ndarray] = None
     row_counts: Optional[np.ndarray] = None
+    sigma_E: Optional[np.ndarray] = None   # every singular value of the merge core E
 
 
 @dataclass
@@ -397,7 +398,7 @@ def isma(A: np.ndarray, p: Params) -> Result:
         U, sig = res.U, res.sigma
         trace.append(IterRecord(t=t, idx=idx, g=int(idx.size), remaining=int(in_S.sum()),
                                 sin_max=sin_max, cos_min=cos_min, sigma=sig.copy(),
-                                rows=rows, row_counts=counts))
+                                rows=rows, row_counts=counts, sigma_E=res.sigma_E.copy()))
         if t > 0 and r_prev >= p.k:
             if p.criterion == "subspace" and sin_max <= p.tol:
                 converged = True

@@ -144,6 +144,7 @@ struct pod_ctx {
     bool modes_done;
     // A^T U on tensor cores (precision POD_PREC_TF32X3)
     int use_tc;
+    uint32_t tc_spin;   // pipeline-wait bound of the tensor-core kernels (0: default)
     AtuTcPlan tcplan;
     double *tc_part;
     unsigned *tc_counters;
@@ -328,6 +329,7 @@ static pod_status enqueue_atu(pod_ctx *c, const DevState *st, const uint8_t *mas
         ta.Y = c->Y;
         ta.counters = c->tc_counters;
         ta.err = &c->st->status;
+        ta.spin = c->tc_spin;
         return launch_atu_tc(ta, c->tcplan, (const float *)c->A, (const float *)c->U, s);
     }
     AtuArgs<T> aa{};
@@ -1181,7 +1183,10 @@ pod_status pod_iterate(pod_ctx *c, int32_t max_steps, int32_t *done, double *sin
     if (done) *done = c->hstate->done;
     if (sin_max) *sin_max = c->hstate->measure;
     if (steps_run) *steps_run = c->hstate->rounds_run - before;
-    if (c->hstate->status != 0) return (pod_status)c->hstate->status;
+    if (c->hstate->status != 0) {
+        c->poisoned = true;   // POD_ENAN, POD_ERANK, POD_ETIMEOUT: the run's state is not usable
+        return (pod_status)c->hstate->status;
+    }
     return POD_OK;
 }
 
@@ -1199,7 +1204,7 @@ pod_status pod_modes(pod_ctx *c, void *U_dev, double *sigma_dev, void *V_dev) {
         if (st == POD_OK) st = read_state(c);
         if (st == POD_OK && c->hstate->status != 0) st = (pod_status)c->hstate->status;
         if (st != POD_OK) {
-            if (st == POD_ECUDA || st == POD_ETIMEOUT) c->poisoned = true;
+            if (st == POD_ECUDA || st == POD_ETIMEOUT || st == POD_ENAN) c->poisoned = true;
             return st;
         }
     }
@@ -1229,7 +1234,7 @@ pod_status pod_get_trace(pod_ctx *c, int32_t t, int32_t *idx_host, int32_t *g_ho
 
 pod_status pod_replay_indices(pod_ctx *c, const int32_t *idx_host, const int32_t *offsets_host, int32_t T) {
     if (!c || !idx_host || !offsets_host || T < 0 || T > c->p.n) return POD_EINVAL;
-    if (c->graph_ready || c->hstate->rounds_run > 0) return POD_ESTATE;
+    if (c->poisoned || c->graph_ready || c->hstate->rounds_run > 0) return POD_ESTATE;
     const int32_t total = offsets_host[T];
     if (offsets_host[0] != 0 || total < 0) return POD_EINVAL;
     for (int t = 0; t < T; ++t) {
@@ -1460,6 +1465,13 @@ pod_status pod_robust_rounds(pod_ctx *c, int32_t *robust_rounds) {
     if (c->poisoned) return POD_ESTATE;
     POD_TRY(read_state(c));
     *robust_rounds = c->hstate->robust_rounds;
+    return POD_OK;
+}
+
+pod_status pod_set_wait_limit(pod_ctx *c, uint32_t polls) {
+    if (!c) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    c->tc_spin = polls;
     return POD_OK;
 }
 

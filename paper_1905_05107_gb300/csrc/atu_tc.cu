@@ -36,7 +36,7 @@ constexpr int TC_KC = 32;                    // rows of A per slab (128 bytes)
 // 1e-6, and the epilogue continues the sum in double-float.
 constexpr int TC_GROUP = 2;
 constexpr int TC_THREADS = 384;
-constexpr uint32_t TC_SPIN = 1u << 24;       // bounded wait: try_wait polls
+constexpr uint32_t TC_SPIN = 1u << 24;       // default bound of a wait: try_wait polls
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -58,10 +58,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false on expiry or when
-// another thread of the CTA has already given up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
-    for (uint32_t it = 0; it < TC_SPIN; ++it) {
+// Bounded wait (at most `limit` polls) for the phase with the given parity;
+// false on expiry or when another thread of the CTA has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_test(b, parity)) return true;
         if (*abort_flag) return false;
     }
@@ -147,6 +147,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int r = st->r_cur;
     if (r <= 0) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // bound of the pipeline waits (the waits for this CTA's own copies and
+    // MMAs after an abort always keep the default bound)
+    const uint32_t lim = a.spin ? a.spin : TC_SPIN;
     const int mt = blockIdx.x, sp = blockIdx.y, splits = gridDim.y;
     const int64_t nslab_all = (a.m + TC_KC - 1) / TC_KC;
     const int64_t per = (nslab_all + splits - 1) / splits;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             for (int kc = 0; kc < nslab && !s_abort; ++kc) {
                 const int s = kc % TC_STAGES;
-                if (kc >= TC_STAGES && !mbar_wait(&freed[s], ((kc / TC_STAGES) - 1) & 1, &s_abort)) break;
+                if (kc >= TC_STAGES && !mbar_wait(&freed[s], ((kc / TC_STAGES) - 1) & 1, &s_abort, lim)) break;
                 mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
                 const int x = (int)((s0 + kc) * TC_KC);
                 tma_2d(stageA(s), &mapA, &full[s], x, mt * 128);
@@ -209,8 +212,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int s = kc % TC_STAGES;
                 const int g = kc / TC_GROUP, b = g & 1;
                 const bool first = (kc % TC_GROUP) == 0;
-                if (first && g >= 2 && !mbar_wait(&drained[b], ((g >> 1) - 1) & 1, &s_abort)) break;
-                if (!mbar_wait(&ready[s], (kc / TC_STAGES) & 1, &s_abort)) break;
+                if (first && g >= 2 && !mbar_wait(&drained[b], ((g >> 1) - 1) & 1, &s_abort, lim)) break;
+                if (!mbar_wait(&ready[s], (kc / TC_STAGES) & 1, &s_abort, lim)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * NT);
                 const uint32_t ah = sa(stageA(s)), al = sa(stageAlo(s));
@@ -229,14 +232,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // (waited for even after an abort: TMEM must not be freed earlier)
             mma_commit(done);
             int never = 0;
-            mbar_wait(done, 0, &never);
+            mbar_wait(done, 0, &never, TC_SPIN);
         }
     } else if (warp >= 4 && warp < 8) {
         // ------------------------------------------------ split hi / lo
         const int t = tid - 128;
         for (int kc = 0; kc < nslab && !s_abort; ++kc) {
             const int s = kc % TC_STAGES;
-            if (!mbar_wait(&full[s], (kc / TC_STAGES) & 1, &s_abort)) break;
+            if (!mbar_wait(&full[s], (kc / TC_STAGES) & 1, &s_abort, lim)) break;
             float4 *ah = reinterpret_cast<float4 *>(stageA(s));
             float4 *al = reinterpret_cast<float4 *>(stageAlo(s));
             float4 *bh = reinterpret_cast<float4 *>(stageB(s));
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < NT; ++c) ahi[c] = alo[c] = 0.f;
         for (int g = 0; g < ngroups && !s_abort; ++g) {
             const int b = g & 1;
-            if (!mbar_wait(&accf[b], (g >> 1) & 1, &s_abort)) break;
+            if (!mbar_wait(&accf[b], (g >> 1) & 1, &s_abort, lim)) break;
             tc_fence_after();
 #pragma unroll
             for (int c0 = 0; c0 < NT; c0 += 32) {
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int issued = s_issued;
             for (int kc = issued > TC_STAGES ? issued - TC_STAGES : 0; kc < issued; ++kc) {
                 int never = 0;
-                mbar_wait(&full[kc % TC_STAGES], (kc / TC_STAGES) & 1, &never);
+                mbar_wait(&full[kc % TC_STAGES], (kc / TC_STAGES) & 1, &never, TC_SPIN);
             }
         }
         __syncthreads();

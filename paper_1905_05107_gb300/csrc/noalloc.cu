@@ -1,19 +1,23 @@
 // pod_sample_noalloc: the column draw step (same kernel as pod_sample) with
 // its scratch in fixed-size device arrays declared in this file, so that the
-// call performs no device allocation at all.
+// call makes no device allocation.
 //
-// Who needs it: code that runs where allocating is not allowed or not
-// possible -- e.g. inside a host callback or another library's stream
-// callback (CUDA forbids CUDA API calls that may allocate there), in a
-// process whose memory pool is capped or already fully reserved by a
-// framework, or in latency-critical loops that must not hit the allocator.
-// Such callers pass their own inputs and outputs and get the scratch from
-// these arrays instead of from cudaMalloc.
+// Who needs it: callers that may not or cannot allocate device memory at the
+// moment they draw -- a process whose device memory pool is capped or already
+// fully reserved by another framework, or a latency-critical loop that must
+// not touch the allocator.  Such callers pass their own inputs and outputs
+// and get the scratch from these arrays instead of from cudaMalloc.  The call
+// itself issues CUDA API calls (an address lookup, copies, a launch), so it
+// must not be made from a host callback (cudaLaunchHostFunc,
+// cudaStreamAddCallback), where CUDA forbids API calls.
 //
 // The arrays live in every GPU that loads this library, for the life of the
-// process (about 1.1 MB each).  All calls share them: two calls that overlap
-// on the GPU (different streams, or different host threads on one device)
-// race on the scratch and must be serialised by the caller.
+// process (about 1.1 MB each).  With CUDA's lazy module loading they are
+// placed in device memory when this file's device code is first used, which
+// is the first call's address lookup: make one call per device at set-up,
+// while allocating is still possible.  All calls share the arrays: two calls
+// that overlap on the GPU (different streams, or different host threads on
+// one device) race on the scratch and must be serialised by the caller.
 #include <mutex>
 
 #include "pod_internal.h"

@@ -201,6 +201,7 @@ struct AtuTcArgs {
     double *Y;              // n x r, ld n
     unsigned *counters;     // one per M-tile, zero between launches
     int *err;               // set to POD_ETIMEOUT when a bounded wait expires
+    uint32_t spin;          // polls before a pipeline wait gives up (0: default)
 };
 struct AtuTcPlan {
     int nt, mtiles, splits;

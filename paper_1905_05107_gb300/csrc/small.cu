@@ -304,6 +304,7 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
 #pragma unroll
     for (int k = 0; k < 4; ++k) off[k] = 4 * ((k + sub) & 3) + lp;
     const float tol2 = tol * tol, loose = 16.f * tol, loose2 = loose * loose;
+    const int max_sweeps0 = max_sweeps;
     int sweep = 0;
     for (;;) {   // a second pass only when the guard below turns the skipping off
     for (;; ++sweep) {
@@ -318,7 +319,10 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
             }
             alpha[c] = s0 + s1;
         }
-        if (tid == 0) s_flag[0] = 0;
+        if (tid == 0) {
+            s_flag[0] = 0;
+            s_thr = 0.f;   // no pair skipped unless a rank below sets it (a NaN norm matches no rank)
+        }
         bar_sync_1(nwork);
         if (sweep >= max_sweeps || ncol < 2) break;
         if (keep_top > 0 && keep_top < ncol) {
@@ -477,7 +481,10 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
             if (alpha[i] + rad >= s_amin) s_bad = 1;
         }
         bar_sync_1(nwork);
-        if (s_bad && sweep < max_sweeps) {
+        if (s_bad) {
+            // sweep every pair from here on; when the skipping used up the
+            // sweep budget, the full sweeps get a budget of their own
+            if (sweep >= max_sweeps) max_sweeps = sweep + max_sweeps0;
             keep_top = 0;
             continue;
         }
@@ -502,58 +509,167 @@ __device__ void sort_desc(const K *key, int n, int *order) {
     __syncthreads();
 }
 
-// Largest singular value of B (nrow x k, column-major, ld): 16 steps of
-// power iteration on B^T B started from its row with the largest diagonal,
-// bounded below by |B|_F / sqrt(k).  One warp does the iteration.
+// Largest singular value of B (nrow x k, column-major, ld), i.e. the square
+// root of the largest eigenvalue of M = B^T B (k x k):
+//  * M is formed and scaled by a power of two to max_i M_ii in [1/2, 1);
+//  * Lanczos with full reorthogonalisation (two classical Gram-Schmidt passes
+//    against every earlier vector per step), started from q_i ~ sqrt(M_ii),
+//    for min(k, LZ_STEPS) steps or until the Krylov space closes; the
+//    reorthogonalised coefficients give the tridiagonal T (alpha, beta);
+//  * the largest eigenvalue of T by multisection with Sturm sign counts
+//    (one warp, 32 points per pass, division-free recurrence with power-of-
+//    two rescaling), clamped to [trace(M) / k, trace(M)], the bounds any
+//    largest eigenvalue of M obeys.
+// Every inner product of a step is split over groups of 8 threads.  B's
+// storage is reused for the Lanczos vectors (B is not needed after M).
+// Work arrays: M k^2, alpha and beta LZ_STEPS + 1 each, wv k, cv 2 (LZ_STEPS
+// + 1).  Called by the whole CTA; the result is valid in threads 0..31.
+constexpr int LZ_STEPS = 64;
+
 template <typename J>
-__device__ double top_singular_value(const J *B, int ld, int nrow, int k, J *BtB, J *x, J *y) {
-    const int tid = threadIdx.x;
-    for (int e = tid; e < k * k; e += blockDim.x) {
+__device__ int sturm_below(const J *al, const J *be, int s, J x) {
+    // number of eigenvalues of T below x: sign changes of the leading minors
+    // P_0 = 1, P_1 = al_0 - x, P_{i+1} = (al_i - x) P_i - be_{i-1}^2 P_{i-1};
+    // a zero minor takes the sign opposite to the one before it
+    const J big = sizeof(J) == 4 ? (J)1e30 : (J)1e250, small_ = sizeof(J) == 4 ? (J)1e-30 : (J)1e-250;
+    const J resc = sizeof(J) == 4 ? (J)1e-30 : (J)1e-250, grow = sizeof(J) == 4 ? (J)1e30 : (J)1e250;
+    J p0 = 1, p1 = al[0] - x;
+    int cnt = 0;
+    bool s0 = true;                       // sign of p0 (true = positive)
+    bool s1 = p1 > (J)0 || (p1 == (J)0 && !s0);
+    cnt += (s1 != s0);
+    for (int i = 1; i < s; ++i) {
+        J p2 = (al[i] - x) * p1 - be[i - 1] * be[i - 1] * p0;
+        const bool s2 = p2 > (J)0 || (p2 == (J)0 && !s1);
+        cnt += (s2 != s1);
+        p0 = p1;
+        p1 = p2;
+        s1 = s2;
+        const J ap = fabs(p1) > fabs(p0) ? fabs(p1) : fabs(p0);
+        if (ap > big) {
+            p0 *= resc;
+            p1 *= resc;
+        } else if (ap < small_ && ap > (J)0) {
+            p0 *= grow;
+            p1 *= grow;
+        }
+    }
+    return cnt;
+}
+
+template <typename J>
+__device__ double top_singular_value(J *B, int ld, int nrow, int k, J *M, J *alpha, J *beta, J *wv, J *cv,
+                                     double *red_d) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int lane8 = tid & 7, grp = tid >> 3, ngrp = bd >> 3;
+    J *red = reinterpret_cast<J *>(red_d);
+    for (int e = tid; e < k * k; e += bd) {
         const int i = e / k, j = e % k;
         J s = 0;
         for (int p = 0; p < nrow; ++p) s = fma(B[(size_t)i * ld + p], B[(size_t)j * ld + p], s);
-        BtB[i * k + j] = s;
+        M[i * k + j] = s;
+    }
+    __syncthreads();
+    J dmax = 0, tr = 0;
+    for (int i = 0; i < k; ++i) {
+        dmax = M[i * k + i] > dmax ? M[i * k + i] : dmax;
+        tr += M[i * k + i];
+    }
+    if (!(dmax > (J)0)) return 0.0;   // B = 0 (or not finite)
+    int ex;
+    frexp((double)dmax, &ex);
+    const J sc = (J)ldexp(1.0, -ex);    // M * sc has max diagonal in [1/2, 1)
+    tr *= sc;
+    __syncthreads();
+    for (int e = tid; e < k * k; e += bd) M[e] *= sc;
+    J *Q = B;                           // Lanczos vectors, k apart
+    const int smax = k < LZ_STEPS ? k : LZ_STEPS;
+    __syncthreads();
+    // q_0 ~ sqrt(M_ii)
+    J nrm0 = 0;
+    for (int i = 0; i < k; ++i) nrm0 += M[i * k + i];   // sum of squares of sqrt(M_ii)
+    const J inv0 = (J)1 / sqrt(nrm0);
+    for (int i = tid; i < k; i += bd) Q[i] = sqrt(M[i * k + i]) * inv0;
+    __syncthreads();
+    const J eps = sizeof(J) == 4 ? (J)1.2e-7 : (J)2.3e-16;
+    int s = 0;
+    for (int j = 0; j < smax; ++j) {
+        const J *qj = Q + (size_t)j * k;
+        // w = M q_j
+        for (int i = grp; i < k; i += ngrp) {
+            J v = 0;
+            for (int l = lane8; l < k; l += 8) v = fma(M[i * k + l], qj[l], v);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if (lane8 == 0) wv[i] = v;
+        }
+        __syncthreads();
+        for (int pass = 0; pass < 2; ++pass) {
+            J *c = cv + pass * (LZ_STEPS + 1);
+            // c_l = q_l^T w, l <= j
+            for (int l = grp; l <= j; l += ngrp) {
+                J v = 0;
+                for (int i = lane8; i < k; i += 8) v = fma(Q[(size_t)l * k + i], wv[i], v);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                if (lane8 == 0) c[l] = v;
+            }
+            __syncthreads();
+            // w -= sum_l c_l q_l
+            for (int i = grp; i < k; i += ngrp) {
+                J v = 0;
+                for (int l = lane8; l <= j; l += 8) v = fma(c[l], Q[(size_t)l * k + i], v);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                if (lane8 == 0) wv[i] -= v;
+            }
+            __syncthreads();
+        }
+        J w2 = 0;
+        for (int i = tid; i < k; i += bd) w2 = fma(wv[i], wv[i], w2);
+        const J bnorm = sqrt(block_sum<J>(w2, red));
+        if (tid == 0) {
+            alpha[j] = cv[j] + cv[LZ_STEPS + 1 + j];
+            beta[j] = bnorm;
+        }
+        s = j + 1;
+        // the Krylov space closed (T's eigenvalues are M's within it)
+        if (!(bnorm > (J)8 * eps * (J)k) || j + 1 == smax) break;
+        const J inv = (J)1 / bnorm;
+        for (int i = tid; i < k; i += bd) Q[(size_t)(j + 1) * k + i] = wv[i] * inv;
+        __syncthreads();
     }
     __syncthreads();
     double result = 0.0;
     if (tid < 32) {
-        J fro = 0, dmax = -1;
-        int imax = 0;
-        for (int i = tid; i < k; i += 32) {
-            const J d = BtB[i * k + i];
-            fro += d;
-            if (d > dmax) { dmax = d; imax = i; }
+        // Gershgorin bounds of T (beta_0 .. beta_{s-2} couple its rows)
+        J lo = alpha[0], hi = alpha[0];
+        for (int i = 0; i < s; ++i) {
+            const J off = (i > 0 ? fabs(beta[i - 1]) : (J)0) + (i + 1 < s ? fabs(beta[i]) : (J)0);
+            lo = alpha[i] - off < lo ? alpha[i] - off : lo;
+            hi = alpha[i] + off > hi ? alpha[i] + off : hi;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            fro += __shfl_xor_sync(0xffffffffu, fro, o);
-            const J od = __shfl_xor_sync(0xffffffffu, dmax, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, imax, o);
-            if (od > dmax || (od == dmax && oi < imax)) { dmax = od; imax = oi; }
+        const int passes = sizeof(J) == 4 ? 6 : 12;
+        for (int ps = 0; ps < passes; ++ps) {
+            const J x = lo + (hi - lo) * (J)(tid + 1) / (J)33;
+            const int cnt = sturm_below<J>(alpha, beta, s, x);
+            const unsigned above = __ballot_sync(0xffffffffu, cnt == s);   // x beyond the top eigenvalue
+            const int l0 = above ? __ffs(above) - 1 : 32;
+            const J xl = __shfl_sync(0xffffffffu, x, l0 > 0 ? l0 - 1 : 0);
+            const J xh = __shfl_sync(0xffffffffu, x, l0 < 32 ? l0 : 31);
+            const J nlo = l0 == 0 ? lo : xl;
+            const J nhi = l0 == 32 ? hi : xh;
+            lo = nlo;
+            hi = nhi;
+            if (hi - lo <= eps * (fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi))) break;
         }
-        for (int i = tid; i < k; i += 32) x[i] = BtB[imax * k + i];
-        __syncwarp();
-        J lam = 0;
-        for (int it = 0; it < 16; ++it) {
-            J nrm = 0, xx = 0;
-            for (int i = tid; i < k; i += 32) {
-                J s = 0;
-                for (int j = 0; j < k; ++j) s = fma(BtB[i * k + j], x[j], s);
-                y[i] = s;
-                nrm = fma(s, s, nrm);
-                xx = fma(x[i], x[i], xx);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-                xx += __shfl_xor_sync(0xffffffffu, xx, o);
-            }
-            __syncwarp();
-            lam = xx > (J)0 ? sqrt(nrm / xx) : (J)0;       // |B^T B x| / |x|
-            const J inv = nrm > (J)0 ? j_rsqrt(nrm) : (J)0;
-            for (int i = tid; i < k; i += 32) x[i] = y[i] * inv;
-            __syncwarp();
-        }
-        const J lower = k > 0 ? fro / (J)k : (J)0;
-        result = sqrt((double)(lam > lower ? lam : lower));
+        J lam = (J)0.5 * (lo + hi);
+        const J lower = tr / (J)k;
+        lam = lam < lower ? lower : (lam > tr ? tr : lam);
+        result = sqrt((double)lam / (double)sc);
     }
     return result;   // valid in threads 0..31
 }
@@ -764,10 +880,12 @@ __host__ __device__ inline CoreLayout core_layout(int rmax, int cmax, int jsize)
     const size_t jb = (jsize == 4 && nmax <= LEAN_LD) ? (size_t)LEAN_LD * nmax : (size_t)nmax * nmax;
     L.phaseB = 2 * al16x(jb * jsize) + al16x((size_t)nmax * jsize) + al16x((size_t)nmax * 4);
     // Vr, Q, Yt: nmax x rmax X; Gb, Rb, Mw, Mb: rmax x rmax X; Bs: nmax x rmax J;
-    // BtB: rmax^2 J; xv, yv: rmax J; sig: rmax X; ord2: rmax int
+    // BtB: rmax^2 J; xv, yv: max(rmax, LZ_STEPS + 1) J; Lanczos work: rmax +
+    // 2 (LZ_STEPS + 1) J; sig: rmax X; ord2: rmax int
+    const size_t lzv = (size_t)(rmax > LZ_STEPS + 1 ? rmax : LZ_STEPS + 1);
     L.phaseC = 3 * al16x((size_t)nmax * rmax * 8) + 4 * al16x((size_t)rmax * rmax * 8) +
-               al16x((size_t)nmax * rmax * jsize) + al16x((size_t)rmax * rmax * jsize) + 2 * al16x((size_t)rmax * jsize) +
-               al16x((size_t)rmax * 8) + al16x((size_t)rmax * 4);
+               al16x((size_t)nmax * rmax * jsize) + al16x((size_t)rmax * rmax * jsize) + 2 * al16x(lzv * jsize) +
+               al16x(((size_t)rmax + 2 * (LZ_STEPS + 1)) * jsize) + al16x((size_t)rmax * 8) + al16x((size_t)rmax * 4);
     const size_t bc = L.phaseB + L.phaseC;
     L.total = L.keep + (L.phaseA > bc ? L.phaseA : bc) + 64;
     return L;
@@ -1048,8 +1166,9 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     X *Mb = cv.take<X>((size_t)a.rmax * a.rmax);
     J *Bs = cv.take<J>((size_t)nmax * a.rmax);
     J *BtB = cv.take<J>((size_t)a.rmax * a.rmax);
-    J *xv = cv.take<J>(a.rmax);
-    J *yv = cv.take<J>(a.rmax);
+    J *xv = cv.take<J>(a.rmax > LZ_STEPS + 1 ? a.rmax : LZ_STEPS + 1);
+    J *yv = cv.take<J>(a.rmax > LZ_STEPS + 1 ? a.rmax : LZ_STEPS + 1);
+    J *lzw = cv.take<J>((size_t)a.rmax + 2 * (LZ_STEPS + 1));
     X *sig = cv.take<X>(a.rmax);
     int *ord2 = cv.take<int>(a.rmax);
     const bool f32 = sizeof(J) == 4;
@@ -1302,7 +1421,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
                 Bs[cidx * nr + p] = (J)XOps<X>::to(Q[cidx * nc + k + p]);
             }
             __syncthreads();
-            const double smax = top_singular_value<J>(Bs, nr, nr, k, BtB, xv, yv);
+            const double smax = top_singular_value<J>(Bs, nr, nr, k, BtB, xv, yv, lzw, lzw + a.rmax, red);
             if (tid == 0) {
                 s_sin = smax;
                 s_measure = smax;

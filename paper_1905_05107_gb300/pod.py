@@ -30,7 +30,7 @@ POD_PREC_F32, POD_PREC_BF16, POD_PREC_BF16X3, POD_PREC_TF32X3 = 0, 1, 2, 3
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
             "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
-            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental", "pod_robust_rounds"]
+            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental", "pod_robust_rounds", "pod_set_wait_limit"]
 
 ROUND_KERNELS = ["sample", "proj", "proj_sum", "cgs_gram", "cgs_sum", "chol1", "qr2_gram", "qr2_sum", "cgs_robust",
                  "chol1_robust", "qr2_robust", "core_svd", "update"]
@@ -87,6 +87,7 @@ def lib():
         L.pod_counters.argtypes = [vp, P(i64), P(i32)]
         L.pod_core_stats.argtypes = [vp, P(i32), P(i64)]
         L.pod_sample_noalloc.argtypes = [vp, vp, i64, i32, u64, i32, i32, vp, vp, vp]
+        L.pod_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
         for name in EXPORTED:
             if name not in ("pod_destroy", "pod_strerror"):
                 getattr(L, name).restype = ctypes.c_int
@@ -291,6 +292,11 @@ class Context:
         out = (ctypes.c_double * 4)()
         _check(lib().pod_wedin(self._h, out), "pod_wedin")
         return {"bound": out[0], "norm_R": out[1], "norm_S": out[2], "omega": out[3]}
+
+    def set_wait_limit(self, polls: int):
+        """Bound of the tensor-core kernels' pipeline waits (pod_set_wait_limit;
+        0 = default)."""
+        _check(lib().pod_set_wait_limit(self._h, int(polls)), "pod_set_wait_limit")
 
     def robust_rounds(self) -> int:
         """Rounds that needed the compensated-Gram rerun of the first CholeskyQR pass."""

@@ -14,6 +14,8 @@ The arrays returned are C-contiguous (n, m) buffers viewed as (m, n) with
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 from typing import Optional
 
@@ -52,6 +54,38 @@ def planted(m: int, n: int, sigma, noise: float, seed: int, dtype=np.float64,
     if noise > 0:
         At += noise * rng.standard_normal((n, m))
     return _finish(At, dtype, center)
+
+
+def planted_large(m: int, n: int, sigma, noise: float, seed: int, dtype=np.float32,
+                  block: int = 256, workers: Optional[int] = None) -> np.ndarray:
+    """The recipe of ``planted`` for matrices too large for one generator to
+    fill quickly: Haar U and V from ``default_rng(seed)``, A = U diag(sigma)
+    V^T + noise * N(0, 1), rows centred in FP64, rounded to ``dtype``.  The
+    noise of snapshot block b (columns [b block, (b + 1) block)) comes from
+    its own generator ``default_rng([seed, 1, b])``, so blocks are filled by
+    parallel threads and the result does not depend on the thread count.
+    Holds one FP64 (n, m) buffer while it works."""
+    rng = np.random.default_rng(seed)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    U = haar(rng, m, sigma.size)
+    V = haar(rng, n, sigma.size)
+    At = np.empty((n, m), dtype=np.float64)
+    nb = (n + block - 1) // block
+
+    def fill_noise(b):
+        part = At[b * block:min(n, (b + 1) * block)]
+        if noise > 0:
+            np.random.default_rng([seed, 1, b]).standard_normal(out=part)
+            part *= noise
+        else:
+            part[...] = 0.0
+
+    with ThreadPoolExecutor(max_workers=workers or os.cpu_count() or 1) as ex:
+        list(ex.map(fill_noise, range(nb)))
+    for b in range(nb):
+        j0, j1 = b * block, min(n, (b + 1) * block)
+        At[j0:j1] += (V[j0:j1] * sigma) @ U.T
+    return _finish(At, dtype, True)
 
 
 def planted_factors(m: int, n: int, sigma, seed: int):
@@ -172,6 +206,22 @@ def diff_sigma() -> np.ndarray:
 def make_diff_c4(seed: int = SEED_DATA + 4, dtype=np.float32, m: int = 200_000, n: int = 1000) -> np.ndarray:
     """The differentiation workload (sizes reducible for quick cases)."""
     return planted(m, n, diff_sigma(), 0.0, seed, dtype)
+
+
+PRECISION_C3 = Workload(
+    "planted-1000000x4000-f32", 1_000_000, 4000, 50, 100, np.float32, 1e-8,
+    "planted sigma_i = exp(-i/15), i = 0..199, Haar U (1e6x200) and V "
+    "(4000x200), N(0, 1e-4^2) noise, rows centred, FP32; k=50, c=100")
+
+
+def precision_sigma() -> np.ndarray:
+    return np.exp(-np.arange(200, dtype=np.float64) / 15.0)
+
+
+def make_precision_c3(seed: int = SEED_DATA + 3, dtype=np.float32, m: int = 1_000_000,
+                      n: int = 4000) -> np.ndarray:
+    """The 16 GB precision workload (sizes reducible for quick cases)."""
+    return planted_large(m, n, precision_sigma(), 1e-4, seed, dtype)
 
 
 def diff_loss_weights(k: int, m: int, seed: int = SEED_DATA + 40):

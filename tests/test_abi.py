@@ -68,3 +68,70 @@ def test_binding_refuses_cpu_tensors():
     A = torch.zeros(4, 3).t().contiguous().t()
     with pytest.raises(ValueError):
         pod._check_colmajor(A)
+
+
+def _good_params():
+    p = pod.PodParams()
+    p.m, p.n, p.lda = 1000, 200, 1000
+    p.k, p.c = 5, 10
+    p.tol = 1e-8
+    return p
+
+
+BAD_PARAMS = [
+    ("m", 0), ("n", 0), ("lda", 999), ("k", 0), ("k", 201), ("c", 0), ("r", 3),
+    ("dtype", 5), ("col_strategy", 7), ("criterion", 3), ("core", 9), ("rows", 2),
+    ("row_strategy", 5), ("w", -1), ("block_trunc", 2), ("precision", 9), ("keep_tape", 2),
+    ("reserved", 1), ("tol", float("nan")),
+]
+
+
+@pytest.mark.parametrize("field,value", BAD_PARAMS)
+def test_init_rejects_bad_parameters(libpath, field, value):
+    """pod_init validates every field before it touches a device, so these
+    run without a GPU: each out-of-range field gives POD_EINVAL and no
+    context."""
+    p = _good_params()
+    setattr(p, field, value)
+    h = ctypes.c_void_p(123)
+    st = pod.lib().pod_init(ctypes.byref(h), ctypes.byref(p), ctypes.c_void_p(0x1000), None)
+    assert st == pod.POD_EINVAL, (field, value, st)
+    assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [("c", 300), ("r", 250), ("keep_tape", 1)])
+def test_init_rejects_unsupported_sizes(libpath, field, value):
+    p = _good_params()
+    setattr(p, field, value)
+    if field == "r":
+        p.c = 100            # r + c beyond the 320-wide core
+    if field == "keep_tape":
+        p.rows = 1           # the adjoint is built for ICS only
+    h = ctypes.c_void_p(0)
+    st = pod.lib().pod_init(ctypes.byref(h), ctypes.byref(p), ctypes.c_void_p(0x1000), None)
+    assert st == pod.POD_EUNSUPPORTED, (field, value, st)
+
+
+def test_null_arguments_are_einval(libpath):
+    L = pod.lib()
+    p = _good_params()
+    assert L.pod_init(None, ctypes.byref(p), ctypes.c_void_p(0x1000), None) == pod.POD_EINVAL
+    h = ctypes.c_void_p(0)
+    assert L.pod_init(ctypes.byref(h), None, ctypes.c_void_p(0x1000), None) == pod.POD_EINVAL
+    assert L.pod_init(ctypes.byref(h), ctypes.byref(p), None, None) == pod.POD_EINVAL
+    assert L.pod_iterate(None, 1, None, None, None) == pod.POD_EINVAL
+    assert L.pod_modes(None, None, None, None) == pod.POD_EINVAL
+    assert L.pod_set_wait_limit(None, 1) == pod.POD_EINVAL
+    assert L.pod_colnorms(None, 0, 10, 10, 10, None, None) == pod.POD_EINVAL
+    assert L.pod_colnorms(ctypes.c_void_p(0x1000), 7, 10, 10, 10, ctypes.c_void_p(0x2000), None) == pod.POD_EINVAL
+    assert L.pod_sample(None, None, 10, 1, 0, 0, 0, None, None, None) == pod.POD_EINVAL
+    assert L.pod_sample_noalloc(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 1 << 20, 4, 0, 0, 0,
+                                ctypes.c_void_p(0x3000), ctypes.c_void_p(0x4000), None) == pod.POD_EUNSUPPORTED
+    L.pod_destroy(None)
+
+
+def test_strerror_covers_every_status(libpath):
+    L = pod.lib()
+    texts = [L.pod_strerror(s) for s in range(9)]
+    assert len(set(texts)) == 9 and b"unknown" not in b"".join(texts)
+    assert L.pod_strerror(99) == b"unknown status"

@@ -67,6 +67,41 @@ def test_backward_planted_f32_matches_autograd():
     assert rel(G, R) < 1e-4, rel(G, R)
 
 
+def _fd_check(A, G, sets, k, c, w, g, directions, seed):
+    """Central differences (h = 1e-3) of the FP64 oracle's loss with the run's
+    draws frozen, along `directions` random unit directions D (Frobenius
+    norm 1): |FD - <dL/dA, D>| <= 1e-3 |dL/dA|_F."""
+    A64 = A.astype(np.float64)
+    rng = np.random.default_rng(seed)
+    h = 1e-3
+
+    def L(X):
+        res = O.isma(X, O.Params(k=k, c=c, seed=0x5107, tol=0.0, replay=sets))
+        return float(np.sum(w * (res.U.T @ g) ** 2))
+
+    gnorm = np.linalg.norm(G)
+    worst = 0.0
+    for _ in range(directions):
+        D = rng.standard_normal(A.shape)
+        D /= np.linalg.norm(D)
+        fd = (L(A64 + h * D) - L(A64 - h * D)) / (2 * h)
+        err = abs(fd - np.sum(G * D))
+        worst = max(worst, err / gnorm)
+        assert err <= 1e-3 * gnorm, (fd, np.sum(G * D))
+    return worst
+
+
+def test_backward_fd_64_directions_reduced():
+    """The differentiation workload's spectrum and loss at m = 20000,
+    n = 200 (k = 16, c = 32, FP32): the GPU adjoint against central finite
+    differences of the FP64 oracle along 64 random directions."""
+    A = synth.make_diff_c4(m=20_000, n=200)
+    k, c = 16, 32
+    w, g = synth.diff_loss_weights(k, A.shape[0])
+    G, sets = gpu_grad(A, k, c, w, g)
+    _fd_check(A, G, sets, k, c, w, g, 64, 11)
+
+
 def test_backward_differentiation_workload_full_size():
     """m = 200000, n = 1000, k = 16, c = 32 (FP32): the GPU adjoint against
     the FP64 autograd reference of the same frozen draws, and against central
@@ -79,15 +114,4 @@ def test_backward_differentiation_workload_full_size():
     A64 = A.astype(np.float64)
     R, _ = Gd.gradient(A64, sets, k, k, w, g)
     assert rel(G, R) < 1e-4, rel(G, R)
-    rng = np.random.default_rng(7)
-    h = 1e-3
-
-    def L(X):
-        res = O.isma(X, O.Params(k=k, c=c, seed=0x5107, tol=0.0, replay=sets))
-        return float(np.sum(w * (res.U.T @ g) ** 2))
-
-    for _ in range(2):
-        D = rng.standard_normal(A.shape)
-        D /= np.linalg.norm(D)
-        fd = (L(A64 + h * D) - L(A64 - h * D)) / (2 * h)
-        assert abs(fd - np.sum(G * D)) <= 1e-3 * np.linalg.norm(G), (fd, np.sum(G * D))
+    _fd_check(A, G, sets, k, c, w, g, 4, 7)

@@ -245,3 +245,84 @@ def test_replay_matches_oracle_replay():
     assert g["steps"] == 5
     np.testing.assert_allclose(g["sigma"], ref.sigma, rtol=1e-10)
     assert sin_max(ref.U, g["U"]) < 1e-10
+
+
+# ----------------------------------------------------------------------- a9
+U32 = 5.96e-8
+
+
+def _measure_bar(ref, t, k, u):
+    """Bar on |GPU measure - oracle measure| in round t: the top-k subspaces
+    compared in that round are each fixed only to about u sigma_1 / gap_k of
+    their merge cores (Davis-Kahan / Wedin), so 10 times the sum of the two
+    floors, plus 1e-9 for the FP64 arithmetic of the measure itself."""
+    def floor(rec):
+        sE = rec.sigma_E
+        if sE is None or sE.size <= k:
+            return 0.0
+        return u * sE[0] / max(sE[k - 1] - sE[k], 1e-300)
+    prev = floor(ref.trace[t - 1]) if t > 0 else 0.0
+    return 10.0 * (floor(ref.trace[t]) + prev) + 1e-9
+
+
+@pytest.mark.parametrize("case", ["planted_f64", "planted_f32", "flow_f32"])
+def test_convergence_measure_trace(case):
+    """Alg. 1's convergence test, subspace form: the per-round max sin(theta)
+    between the previous and the merged top-k modes, compared round by round
+    with the oracle's (1.0 where no comparison exists yet).  FP64 data:
+    within 1e-9; FP32 data: within the per-round floor of _measure_bar."""
+    if case == "planted_f64":
+        A, k, c, u = synth.make_planted_small(), 10, 20, 1.11e-16
+    elif case == "planted_f32":
+        A, k, c, u = synth.make_planted_small(dtype=np.float32), 10, 20, U32
+    else:
+        A, k, c, u = synth.make_flow_316(grid=100, n=600), 20, 40, U32
+    ref = O.isma(A.astype(np.float64), oracle_params(k, c, tol=1e-8))
+    g = run_gpu(A, k, c, tol=1e-8)
+    assert g["steps"] == len(ref.trace)
+    compared = 0
+    for t, rec in enumerate(ref.trace):
+        bar = 1e-9 if u < 1e-15 else _measure_bar(ref, t, k, u)
+        assert abs(g["measure"][t] - rec.sin_max) <= bar, (t, g["measure"][t], rec.sin_max, bar)
+        compared += rec.sin_max < 1.0
+    assert compared >= len(ref.trace) - 2
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-8), (np.float32, 1e-4)])
+def test_subspace_criterion_stops_before_s_is_empty(dtype, tol):
+    """A noiseless planted matrix of rank k: once the sampled columns span its
+    column space (round 2 with c = 2, k = 6) the next merge leaves the top-k
+    subspace unchanged, max sin(theta) falls below tol and Alg. 1 stops with
+    most columns unsampled.  Steps, the done flag, every draw and the final
+    measure agree with the oracle."""
+    k, c = 6, 2
+    A = synth.planted(2000, 300, 0.7 ** np.arange(k), 0.0, 99, dtype)
+    ref = O.isma(A.astype(np.float64), oracle_params(k, c, tol=tol))
+    assert ref.converged and ref.trace[-1].remaining > 250 and len(ref.trace) == 4
+    g = run_gpu(A, k, c, tol=tol)
+    assert g["done"] and g["steps"] == len(ref.trace)
+    for t, rec in enumerate(ref.trace):
+        assert np.array_equal(g["idx"][t], rec.idx)
+    assert g["measure"][-1] <= tol
+    assert all(mv == 1.0 for mv in g["measure"][:-1])
+    np.testing.assert_allclose(g["sigma"], ref.sigma, rtol=1e-10 if dtype == np.float64 else 1e-5)
+
+
+def test_merge_core_cut_inside_degenerate_pair():
+    """The flow snapshots' singular values come in exactly degenerate pairs
+    (noise splits them by ~1e-3 of sigma_20 at most); with k = r = 21 every merge core is
+    cut inside the eleventh pair, so the trailing rows of the core's Jacobi
+    hold a direction as large as the last kept one and the Gershgorin guard
+    of the skipped trailing pairs must send the sweeps back over every pair.
+    Draws bit-exact; all 21 singular values and the well-separated top-20
+    subspace (Alg. 2, SVD of the core) at the FP32 bar; sigma_21 and
+    sigma_22 stay within the pair's noise split of the oracle."""
+    A = synth.make_flow_316(grid=100, n=600)
+    k, c = 21, 40
+    ref = O.isma(A.astype(np.float64), oracle_params(k, c, tol=1e-8))
+    g = run_gpu(A, k, c, tol=1e-8)
+    assert g["steps"] == len(ref.trace)
+    for t, rec in enumerate(ref.trace):
+        assert np.array_equal(g["idx"][t], rec.idx), "round %d" % t
+    np.testing.assert_allclose(g["sigma"], ref.sigma, rtol=1e-5)
+    assert sin_max(ref.U[:, :20], g["U"][:, :20]) <= 1e-5

@@ -160,3 +160,88 @@ def test_sign_reference_range():
     z = O.sign_reference(5, 1000)
     assert z.min() >= -1.0 and z.max() < 1.0
     assert abs(z.mean()) < 0.1
+
+
+def test_eq5_row_count_hand_computed():
+    """Eq. 5, c = w = k^2 (1 + sqrt(log(2 / delta)))^2 / epsilon^4 (natural
+    log), worked by hand for epsilon = delta = 0.6 (the YF row of the paper's
+    parameter table):
+      log(2 / 0.6) = 1.2039728, sqrt = 1.0972569, (1 + 1.0972569)^2 = 4.3984866,
+      0.6^4 = 0.1296;
+      k = 5 : 25 * 4.3984866 / 0.1296 = 848.47  -> 849
+      k = 20: 400 * 4.3984866 / 0.1296 = 13575.6 -> 13576
+      k = 2 : 4 * 4.3984866 / 0.1296 = 135.76   -> 136."""
+    assert O.rows_eq5(5, 0.6, 0.6) == 849
+    assert O.rows_eq5(20, 0.6, 0.6) == 13576
+    assert O.rows_eq5(2, 0.6, 0.6) == 136
+
+
+def test_eq3_column_count_hand_computed():
+    """Eq. 3, c = 4 k (1 + sqrt(8 log(1 / delta)))^2 / epsilon^2, by hand for
+    k = 5, epsilon = delta = 0.6: log(1 / 0.6) = 0.5108256, 8x = 4.0866049,
+    sqrt = 2.0215353, (1 + 2.0215353)^2 = 9.1296759, 20 * 9.1296759 / 0.36 =
+    507.20 -> 508."""
+    assert O.columns_eq3(5, 0.6, 0.6) == 508
+
+
+def _capture_row_values(monkeypatch):
+    seen = {}
+    real = O.sample_scale_rows
+
+    def spy(D, row_values, w, seed, t):
+        seen["values"] = np.array(row_values, copy=True)
+        out = real(D, row_values, w, seed, t)
+        seen["rows"], seen["counts"] = out[1], out[2]
+        return out
+
+    monkeypatch.setattr(O, "sample_scale_rows", spy)
+    return seen
+
+
+def test_leverage_row_values_closed_form(monkeypatch):
+    """Leverage-score row probabilities (Sec. 3.1, Table 2: q_i = |u^i|^2 / k
+    over the first k current modes).  U carries r = 4 > k = 2 modes: its
+    first two columns live on rows 0..3 as the orthonormal pair
+    (1, 1, 1, 1) / 2 and (1, -1, 1, -1) / 2, so each of those rows has
+    |u^i|^2 = 1/4 + 1/4 and q_i = 1/4; the extra modes live on rows 10 and
+    11 and must not count.  D is zero on rows 0..3 and large elsewhere, so
+    row values taken from D, or from all r columns of U, would differ."""
+    m, n = 40, 12
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((m, n))
+    A[0:4, :] = 0.0
+    U = np.zeros((m, 4))
+    U[0:4, 0] = 0.5
+    U[0:4, 1] = [0.5, -0.5, 0.5, -0.5]
+    U[10, 2] = 1.0
+    U[11, 3] = 1.0
+    seen = _capture_row_values(monkeypatch)
+    p = O.Params(k=2, c=3, r=4, rows=1, w=64, row_strategy="ls")
+    O.new_block(A, np.array([1, 5, 7]), p, 1, U)
+    want = np.zeros(m)
+    want[0:4] = 0.25
+    np.testing.assert_array_equal(seen["values"], want)
+    # all draws on rows 0..3; the four weights are equal, so draw j picks
+    # support row floor(u_j * 4 / 2^64) (the selection rule on equal weights)
+    us = O.uniform_u64(p.seed, 1, O.STREAM_ROWS, p.w)
+    expect = np.bincount([(u * 4) >> 64 for u in us], minlength=4)
+    np.testing.assert_array_equal(seen["rows"], np.flatnonzero(expect))
+    np.testing.assert_array_equal(seen["counts"], expect[expect > 0])
+
+
+def test_leverage_rows_fall_back_to_d_norms_without_modes(monkeypatch):
+    """Round 0 has no modes: the LS strategy takes the L2 norms of D's rows
+    (Alg. 1, GET UPDATE with rows), here a closed form for a D with two
+    non-zero rows."""
+    m, n = 30, 6
+    A = np.zeros((m, n))
+    A[4, :] = 2.0
+    A[9, :] = [1.0, 0, 0, 3.0, 0, 0]
+    seen = _capture_row_values(monkeypatch)
+    p = O.Params(k=2, c=2, rows=1, w=16, row_strategy="ls")
+    O.new_block(A, np.array([0, 3]), p, 0, np.zeros((m, 0)))
+    want = np.zeros(m)
+    want[4] = 8.0
+    want[9] = 10.0
+    np.testing.assert_array_equal(seen["values"], want)
+    assert set(seen["rows"].tolist()) <= {4, 9}

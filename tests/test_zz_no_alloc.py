@@ -50,6 +50,36 @@ def test_noalloc_sampler_matches_allocating_entry_point_twice(n, c):
         assert np.array_equal(new_mask, ref_mask), "call %d" % call
 
 
+def test_noalloc_sampler_leaves_device_memory_unchanged():
+    """After the first call on the device (which looks up, and under lazy
+    module loading places, the fixed arrays), further calls change neither
+    the device's free memory nor what the caching allocator holds."""
+    L = pod.lib()
+    n, c = 4000, 64
+    w = torch.ones(n, dtype=torch.int64, device=DEV)
+    mask = torch.ones(n, dtype=torch.uint8, device=DEV)
+    idx = torch.zeros(c, dtype=torch.int32, device=DEV)
+    g = torch.zeros(1, dtype=torch.int32, device=DEV)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(DEV).cuda_stream)
+
+    def call(t):
+        st = L.pod_sample_noalloc(ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(mask.data_ptr()), n, c, 1, t, 0,
+                                  ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(g.data_ptr()), stream)
+        assert st == pod.POD_OK, pod.strerror(st)
+
+    call(0)                                  # set-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    held0 = torch.cuda.memory_reserved(DEV)
+    for t in range(1, 4):
+        mask.fill_(1)
+        call(t)
+    torch.cuda.synchronize()
+    assert int(g.item()) > 0
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert free1 == free0 and torch.cuda.memory_reserved(DEV) == held0
+
+
 def test_noalloc_sampler_rejects_sizes_beyond_its_arrays():
     L = pod.lib()
     n = (1 << 16) + 1
