@@ -2,31 +2,37 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Workload (the FP32 configuration of the method's benchmark): synthetic
-flow-like snapshots on a 316 x 316 grid (m = 99856) x n = 2000 time steps,
-60 separable travelling waves with amplitudes j^-1.5 plus N(0, 1e-3^2)
-noise, rows centred; k = 20 modes, c = 40 columns per iteration, uniform
-sampling after the column-norm round, subspace tolerance 1e-8 (the loop runs
-until every column is merged), closing refinement QR(A^T U), SVD(R).
+Headline workload (the largest single-GPU configuration of the method's
+benchmark set): planted-1000000x4000-f32, a planted spectrum
+sigma_i = exp(-i/15) over 200 modes (Haar factors) plus N(0, 1e-4^2) noise,
+rows centred, stored FP32 (16 GB); k = 50 modes, c = 100 columns per
+iteration, uniform sampling after the column-norm round, subspace tolerance
+1e-8 (the loop runs until every column is merged), closing refinement
+QR(A^T U), SVD(R).  The FP32 flow workload (316 x 316 grid x 2000
+snapshots, k = 20, c = 40) is timed beside it under "flow_316".
 
 One step = one whole problem: pod_reset (column norms, state) + every ISMA
 round + pod_modes (refinement, sign fix, copy-out).  `value` is the device
-time of a step with A resident in HBM (0.8 GB, larger than the 129 MB L2, so
-no flush between steps); `e2e` is the same step through the C ABI with the
-host->device copy of A from pinned memory and the device->host copy of U and
-sigma inside the timed region.
+time of a step with A resident in HBM (16 GB, far larger than the 129 MB L2,
+so no flush between steps); `e2e` is the same step through the C ABI with
+the host->device copy of A from pinned memory and the device->host copy of
+U and sigma inside the timed region.
 
 N > 1 (torchrun): independent replicas, one problem per GPU, no collective
 on the data path; the timed region is bracketed by a barrier and the max
 over ranks is reported.
 
 --impl reference times the FP64 CPU oracle (oracle/isma.py) on the host
-cores on a bounded sample of the same problem (see `cpu_baseline.sample`).
+cores.  Each step runs the next few units of the problem (column norms, one
+ISMA round each, the refinement), resuming where the previous step stopped
+and starting over after the refinement, so that the timed steps cover the
+whole problem; `value` adds up the measured units of one complete problem.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -39,22 +45,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-K_MODES, C_DRAWS, TOL = 20, 40, 1e-8
 METRIC = "time-to-k-POD-modes (s)"
-WORKLOAD = "flow-316x316x2000-f32"
+SEED_SAMPLING = 0x5107
+HEAD = dict(workload="planted-1000000x4000-f32", k=50, c=100, tol=1e-8)
+FLOW = dict(workload="flow-316x316x2000-f32", k=20, c=40, tol=1e-8)
 
 # FP32 SIMT peak of a GB300 from its unit counts and clock: 152 SMs x 128
 # FP32 lanes x 2 flop (FMA) x 2.07 GHz; and the same for one SM.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP32_SM_PEAK_GFLOPS = 128 * 2 * 2.07e9 / 1e9
+# nominal dense TF32 / BF16 tensor rate ratio (1.1 / 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
 
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the kernel as it was when captured; the hash of
 # its sources at that time guards against reporting stale counters.
-NCU_TRAFFIC = {
-    # profiles/k_core_flow316x316x2000_f32.md: 281.6 KB read, 0 written
-    "core_svd": {"bytes": 281600, "src_sha": "e1e94b5850f01494"},
-}
+NCU_TRAFFIC = {}
 KERNEL_SOURCES = {
     "core_svd": ["paper_1905_05107_gb300/csrc/small.cu", "paper_1905_05107_gb300/csrc/common.cuh",
                  "paper_1905_05107_gb300/csrc/pod_internal.h"],
@@ -112,13 +118,15 @@ def ncu_traffic(kernel):
 
 
 def load_peaks():
+    """(HBM GB/s, BF16 dense TFLOP/s burst, BF16 sustained, source)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", 1902.8)), "measured"
+        return (float(d["hbm_gbs"]), float(d.get("bf16_tflops", 1902.8)),
+                float(d.get("bf16_tflops_sustained", d.get("bf16_tflops", 1710.0))), "measured")
     except Exception:
-        return 6800.0, 1900.0, "fallback"
+        return 6800.0, 1900.0, 1700.0, "fallback"
 
 
 class ClockSampler:
@@ -166,68 +174,113 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make_input():
+def make_head():
     from paper_1905_05107_gb300 import synth
-    return synth.make_flow_316()          # (m, n) Fortran-ordered float32
+    return synth.make_precision_c3()      # (m, n) Fortran-ordered float32
 
 
-# ---------------------------------------------------------------- CPU oracle
-def oracle_sample(A, rounds_total, sample_rounds=3):
-    """The FP64 oracle on a bounded sample of the problem: column norms and
-    the refinement are timed in full; `sample_rounds` ISMA rounds are timed
-    and scaled to the rounds the whole problem needs."""
-    from oracle import isma as O
-    A64 = A.astype(np.float64)
-    t0 = time.perf_counter()
-    O.column_sq_norms(A64)
-    t_norms = time.perf_counter() - t0
-    p = O.Params(k=K_MODES, c=C_DRAWS, tol=TOL, refine=False, max_iter=sample_rounds - 1, seed=0x5107)
-    t0 = time.perf_counter()
-    res = O.isma(A64, p)
-    t_isma = time.perf_counter() - t0
-    t_round = max(t_isma - t_norms, 0.0) / max(len(res.trace), 1)
-    t0 = time.perf_counter()
-    O.refine(A64, res.U)
-    t_ref = time.perf_counter() - t0
-    value = t_norms + rounds_total * t_round + t_ref
-    return value, dict(t_norms=t_norms, t_round=t_round, t_refine=t_ref, rounds=len(res.trace))
+def make_flow():
+    from paper_1905_05107_gb300 import synth
+    return synth.make_flow_316()
 
 
 def cpu_cores():
     return os.cpu_count() or 1
 
 
+def floor_u(sig_E_like, k, u):
+    """Predicted accuracy floor u sigma_1 / (sigma_k - sigma_{k+1})."""
+    s = np.asarray(sig_E_like)
+    if s.size <= k:
+        return None
+    return float(u * s[0] / max(s[k - 1] - s[k], 1e-300))
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_params(w):
+    from oracle import isma as O
+    return O.Params(k=w["k"], c=w["c"], tol=w["tol"], refine=True, seed=SEED_SAMPLING)
+
+
+def oracle_full(A, w):
+    """One whole FP64 oracle run on the host cores: (seconds, Result)."""
+    from oracle import isma as O
+    A64 = np.asarray(A, dtype=np.float64)
+    t0 = time.perf_counter()
+    res = O.isma(A64, oracle_params(w))
+    return time.perf_counter() - t0, res
+
+
 def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores, in bounded steps that
+    together cover the whole problem (see the module docstring)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    A = make_input()
-    # rounds of the whole problem: UNF draws until S is empty (identical on
-    # every implementation); counted with the oracle's sampler alone
     from oracle import isma as O
-    n = A.shape[1]
+    A = make_head()
+    A64 = np.asarray(A, dtype=np.float64)
+    del A
+    m, n = A64.shape
+    # units of one problem: column norms, T rounds, refinement; T from the
+    # draws alone (UNF after round 0 until S is empty; identical on every
+    # implementation)
     in_S = np.ones(n, dtype=bool)
-    s = O.column_sq_norms(A.astype(np.float64))
+    s = O.column_sq_norms(A64)
     rounds = 0
     while in_S.any():
         vals = s if rounds == 0 else np.ones(n)
-        idx, _ = O.sample_columns(vals, in_S, C_DRAWS, 0x5107, rounds)
+        idx, _ = O.sample_columns(vals, in_S, HEAD["c"], SEED_SAMPLING, rounds)
         in_S[idx] = False
         rounds += 1
-    times = []
-    for i in range(args.warmup + args.steps):
-        v, parts = oracle_sample(A, rounds)
-        if i >= args.warmup:
-            times.append(v)
-    value = float(np.mean(times))
-    sample = ("FP64 NumPy/LAPACK oracle on the host: column norms and refinement in full, %d of %d "
-              "ISMA rounds timed and scaled; mean of %d steps" % (parts["rounds"], rounds, args.steps))
+    units_total = rounds + 2
+    per_step = max(1, math.ceil(units_total / max(args.steps, 1)))
+    gen = [None]
+    pos = [0]
+
+    def next_unit():
+        if gen[0] is None:
+            gen[0] = O.isma_steps(A64, oracle_params(HEAD))
+            pos[0] = 0
+        t0 = time.perf_counter()
+        kind, _ = next(gen[0])
+        dt = time.perf_counter() - t0
+        u = pos[0]
+        pos[0] += 1
+        if kind == "done":
+            gen[0] = None
+        return u, dt
+
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            next_unit()
+    measured = {}
+    step_s = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            u, dt = next_unit()
+            measured.setdefault(u, dt)
+        step_s.append(time.perf_counter() - t0)
+    covered = len(measured)
+    if covered >= units_total:
+        value = float(sum(measured[u] for u in range(units_total)))
+        how = "every unit measured"
+    else:
+        rmean = np.mean([measured[u] for u in measured if 0 < u < units_total - 1] or [0.0])
+        value = float(sum(measured.values()) + rmean * (units_total - covered))
+        how = "%d of %d units measured, the rest at the measured mean round time" % (covered, units_total)
+    sample = ("FP64 NumPy/LAPACK oracle (Algorithm 1 with its QR and SVD steps from LAPACK) on %d host "
+              "cores; the problem is cut into %d units (column norms, %d rounds, refinement), each step runs "
+              "the next %d, resuming the previous step's state; value = one whole problem's units (%s)"
+              % (cpu_cores(), units_total, rounds, per_step, how))
+    ms = 1e3 * float(np.mean(step_s))
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "m": int(A.shape[0]), "n": int(A.shape[1]), "k": K_MODES,
-                       "c": C_DRAWS, "rounds": rounds},
+            "config": {"workload": HEAD["workload"], "m": int(m), "n": int(n), "k": HEAD["k"], "c": HEAD["c"],
+                       "tol": HEAD["tol"], "rounds": rounds, "strategy": "L2N round 0, UNF after"},
             "cpu_baseline": {"value": value, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -236,69 +289,64 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def kernel_model(m, n, es, r, g):
-    """Algorithmic bytes and flops per launch (what the method must move)."""
+def kernel_model(m, es, r, g):
+    """Algorithmic bytes and flops per launch of the round's streaming passes
+    (what the method must move)."""
     return {
-        "colnorms": (m * n * es + n * 8, 2.0 * m * n),
         "proj": (m * (r + g) * es, 2.0 * m * r * g),
         "cgs_gram": (m * (r + g) * es, 4.0 * m * r * g + 1.0 * m * g * g),
-        "qr2_gram": (m * (r + g) * es, 4.0 * m * r * g + 2.0 * m * g * g),
+        "qr2_gram": (m * (r + g) * es + m * g * es, 4.0 * m * r * g + 2.0 * m * g * g),
         "update": (m * (r + g) * es + m * r * es, 2.0 * m * (r + g) * r),
     }
 
 
-def run_ours(args):
-    import torch
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
-    from paper_1905_05107_gb300 import build, pod
-    build.build()
-    A_np = make_input()
+def time_problem(torch, pod, A_np, w, steps, warmup, dev, world, detail):
+    """Device-timed and end-to-end steps of one workload; with `detail`, also
+    per-kernel timings, core statistics and the refinement's A^T U."""
     m, n = A_np.shape
-    es = 4
+    k = w["k"]
     A_host = torch.from_numpy(np.ascontiguousarray(A_np.T)).pin_memory()   # (n, m) = column-major A
     A_dev_t = A_host.to(dev)
     A = A_dev_t.t()
     stream = torch.cuda.Stream(dev)
+    out = {}
     with torch.cuda.stream(stream):
-        ctx = pod.Context(A, K_MODES, C_DRAWS, tol=TOL, stream=stream)
+        ctx = pod.Context(A, k, w["c"], tol=w["tol"], stream=stream)
 
         def step():
             ctx.reset()
             ctx.iterate()
             return ctx.modes()
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         rounds = ctx.counters()[1]
-        # ------------------------------------------------ device-timed steps
         barrier(world)
         torch.cuda.synchronize()
-        clocks = ClockSampler(dev.index)
-        clocks.start()
+        clocks = ClockSampler(dev.index) if detail else None
+        if clocks:
+            clocks.start()
         l0, _ = ctx.counters()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             U, sigma, _ = step()
         e1.record(stream)
         torch.cuda.synchronize()
         l1, _ = ctx.counters()
-        clk = clocks.stop()
-        ms = e0.elapsed_time(e1) / args.steps
-        ms = max_over_ranks(ms, world, dev)
+        out["clocks"] = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1) / steps
+        out["ms"] = max_over_ranks(ms, world, dev)
+        out["launches"] = (l1 - l0) // steps
+        out["rounds"] = rounds
+        out["U"] = U.double().cpu().numpy()
+        out["sigma"] = sigma.cpu().numpy()
         barrier(world)
-        launches = (l1 - l0) // args.steps
         # ------------------------------------------------ end-to-end steps
-        U_host = torch.empty((K_MODES, m), dtype=torch.float32).pin_memory()
-        s_host = torch.empty(K_MODES, dtype=torch.float64).pin_memory()
+        U_host = torch.empty((k, m), dtype=torch.float32).pin_memory()
+        s_host = torch.empty(k, dtype=torch.float64).pin_memory()
 
         def step_e2e():
             A_dev_t.copy_(A_host, non_blocking=True)
@@ -312,117 +360,173 @@ def run_ours(args):
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step_e2e()
         f1.record(stream)
         torch.cuda.synchronize()
-        ms_e2e = f0.elapsed_time(f1) / args.steps
-        ms_e2e = max_over_ranks(ms_e2e, world, dev)
-        # ------------------------------------------------ per-kernel timings
-        # one more run, round by round, with CUDA events between kernels
-        ctx.reset()
-        per = {}
-        rg = []
-        sweeps, core_cyc = [], []
-        for t in range(rounds):
-            for kname, v in ctx.round_timings().items():
-                per.setdefault(kname, []).append(v)
-            rg.append(len(ctx.trace(t)[0]))
-            sw, cyc = ctx.core_stats()
-            sweeps.append(sw)
-            core_cyc.append(cyc)
-        ctx.modes()
-        cn = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        torch.cuda.synchronize()
-        cn[0].record(stream)
-        reps = 5
-        for _ in range(reps):
-            pod.colnorms(A, stream=stream)
-        cn[1].record(stream)
-        torch.cuda.synchronize()
-        per["colnorms"] = [cn[0].elapsed_time(cn[1]) / reps]
-        # refinement + copy-out, once
-        ctx.reset()
-        ctx.iterate()
-        mm = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        mm[0].record(stream)
-        ctx.modes()
-        mm[1].record(stream)
-        torch.cuda.synchronize()
-        per["modes_refine"] = [mm[0].elapsed_time(mm[1])]
+        out["ms_e2e"] = max_over_ranks(f0.elapsed_time(f1) / steps, world, dev)
+        out["h2d"] = int(m * n * 4)
+        out["d2h"] = int(m * k * 4 + k * 8)
+        if detail:
+            # one more run, round by round, with CUDA events between kernels
+            ctx.reset()
+            per, rg, sweeps, core_cyc = {}, [], [], []
+            for t in range(rounds):
+                for kname, v in ctx.round_timings().items():
+                    per.setdefault(kname, []).append(v)
+                rg.append(len(ctx.trace(t)[0]))
+                sw, cyc = ctx.core_stats()
+                sweeps.append(sw)
+                core_cyc.append(cyc)
+            ref = ctx.refine_timings()
+            ctx.modes()
+            per["refine_atu"] = [ref["atu"]]
+            per["refine_rest"] = [sum(v for kk, v in ref.items() if kk != "atu")]
+            cn = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            cn[0].record(stream)
+            reps = 3
+            for _ in range(reps):
+                pod.colnorms(A, stream=stream)
+            cn[1].record(stream)
+            torch.cuda.synchronize()
+            per["colnorms"] = [cn[0].elapsed_time(cn[1]) / reps]
+            out.update(per=per, rg=rg, sweeps=sweeps, core_cyc=core_cyc)
         ctx.close()
+    del A_dev_t, A_host
+    torch.cuda.empty_cache()
+    return out
 
+
+def roofline_of(t, m, n, k, hbm, bf16):
+    """The dominant kernel's roofline plus the streaming and tensor-core
+    kernels' fractions, from the per-kernel timings of one run."""
+    per, rg, sweeps = t["per"], t["rg"], t["sweeps"]
+    es = 4
     totals = {kname: float(np.sum(v)) for kname, v in per.items()}
     dominant = max(totals, key=totals.get)
-    hbm, bf16, peak_kind = load_peaks()
-    # algorithmic bytes of every launch of each streaming kernel (round t has
-    # r_t = 0 modes in round 0 and K_MODES after, g_t distinct columns)
-    moved = {}
-    for t, g in enumerate(rg):
-        mdl = kernel_model(m, n, es, 0 if t == 0 else K_MODES, g)
+    moved, flops = {}, {}
+    for i, g in enumerate(rg):
+        mdl = kernel_model(m, es, 0 if i == 0 else k, g)
         for kname in ("proj", "cgs_gram", "qr2_gram", "update"):
             moved[kname] = moved.get(kname, 0.0) + mdl[kname][0]
-    moved["colnorms"] = kernel_model(m, n, es, K_MODES, C_DRAWS)["colnorms"][0] * len(per["colnorms"])
+            flops[kname] = flops.get(kname, 0.0) + mdl[kname][1]
+    moved["colnorms"] = float(m * n * es + n * 8)
+    moved["refine_atu"] = float(m * n * es + m * k * es)
     hbm_kernels = {}
     for kname, b in moved.items():
+        if kname not in totals or totals[kname] <= 0:
+            continue
         gbs = b / (totals[kname] * 1e-3) / 1e9
         hbm_kernels[kname] = {"GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4)}
-    # the core SVD: one CTA, one-sided Jacobi on the (r + g)-wide core;
-    # algorithmic flops 6 n_c^3 per sweep (n_c = r_t + g_t)
+    # tensor pipe of the refinement's A^T U: 3 split-TF32 products of 2 m n k
+    tf32_peak = bf16 * TF32_PER_BF16
+    atu_tflops = 3 * 2.0 * m * n * k / (totals["refine_atu"] * 1e-3) / 1e12
+    tensor = {"refine_atu": {"TFLOP/s": round(atu_tflops, 1), "peak": round(tf32_peak, 1),
+                             "frac": round(atu_tflops / tf32_peak, 4),
+                             "note": "split TF32 (3 products); peak = BF16 peak x nominal TF32/BF16 ratio"}}
     core_flops = 0.0
-    for t, g in enumerate(rg):
-        nc = (0 if t == 0 else K_MODES) + g
-        core_flops += 6.0 * nc ** 3 * (sweeps[t] if t < len(sweeps) else 0)
+    for i, g in enumerate(rg):
+        nc = (0 if i == 0 else k) + g
+        core_flops += 6.0 * nc ** 3 * (sweeps[i] if i < len(sweeps) else 0)
     if dominant == "core_svd":
         launches_k = len(per["core_svd"])
         avg_ms = totals["core_svd"] / launches_k
         achieved = core_flops / launches_k / (avg_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": "core_svd", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ncu_traffic("core_svd"),
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (FP32 FMA)",
-                    "algorithmic_flops_per_launch": core_flops / launches_k, "avg_launch_ms": avg_ms,
-                    "note": "one CTA on one of 152 SMs, latency-bound Jacobi rounds; frac of that SM's "
-                            "FP32 peak: %.4f" % (achieved * 1e3 / FP32_SM_PEAK_GFLOPS)}
+        roof = {"bound": "alu", "kernel": "core_svd", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ncu_traffic("core_svd"),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (FP32 FMA)",
+                "algorithmic_flops_per_launch": core_flops / launches_k, "avg_launch_ms": avg_ms,
+                "note": "one CTA on one of 152 SMs, latency-bound Jacobi rounds; frac of that SM's "
+                        "FP32 peak: %.4f" % (achieved * 1e3 / FP32_SM_PEAK_GFLOPS)}
     else:
-        roof_kernel = dominant if dominant in moved else max((k for k in totals if k in moved), key=totals.get)
+        roof_kernel = dominant if dominant in moved else max((kk for kk in totals if kk in moved), key=totals.get)
         launches_k = len(per[roof_kernel])
         avg_ms = totals[roof_kernel] / launches_k
         bytes_ = moved[roof_kernel] / launches_k
         achieved = bytes_ / (avg_ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": roof_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": ncu_traffic(roof_kernel),
-                    "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs" % peak_kind,
-                    "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms}
-    roofline["time_share"] = {k: round(totals[k] / sum(totals.values()), 4) for k in totals}
-    roofline["dominant_kernel"] = dominant
-    roofline["hbm_kernels"] = hbm_kernels
-    core_phase = np.mean(np.array(core_cyc, dtype=np.float64), axis=0).tolist() if core_cyc else []
+        roof = {"bound": "hbm", "kernel": roof_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": ncu_traffic(roof_kernel),
+                "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms}
+    roof["time_share"] = {kk: round(totals[kk] / sum(totals.values()), 4) for kk in totals}
+    roof["dominant_kernel"] = dominant
+    roof["hbm_kernels"] = hbm_kernels
+    roof["tensor_kernels"] = tensor
+    return roof
 
-    cpu = None
+
+def accuracy(U, sigma, ref, k):
+    """sigma relative errors and sin(theta) of the top-j subspaces against the
+    oracle, with the FP32 floor u sigma_1 / gap_j of the oracle's spectrum."""
+    from oracle import isma as O
+    u32 = 5.96e-8
+    rel = np.abs(sigma - ref.sigma) / ref.sigma
+    sall = ref.sigma_all if ref.sigma_all is not None else ref.sigma
+    out = {"sigma_rel_max": float(rel.max())}
+    for j in sorted({10, 20, 30, 40, k}):
+        if j > k:
+            continue
+        out["sin_top%d" % j] = float(O.sin_principal_max(ref.U[:, :j], U[:, :j]))
+        out["floor_top%d" % j] = floor_u(sall, j, u32)
+    out["sigma_rel_top20"] = float(rel[:20].max())
+    return out
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1905_05107_gb300 import build, pod
+    build.build()
+    A_np = make_head()
+    m, n = A_np.shape
+    k = HEAD["k"]
+    t = time_problem(torch, pod, A_np, HEAD, args.steps, args.warmup, dev, world, detail=True)
+    hbm, bf16, bf16_sus, peak_kind = load_peaks()
+    roof = roofline_of(t, m, n, k, hbm, bf16)
+    roof["peak_source"] = roof.get("peak_source", "%s: MEASURED_PEAKS.json hbm_gbs" % peak_kind)
+    core_phase = np.mean(np.array(t["core_cyc"], dtype=np.float64), axis=0).tolist()
+    # the FP32 flow workload beside it
+    F_np = make_flow()
+    tf = time_problem(torch, pod, F_np, FLOW, args.steps, args.warmup, dev, world, detail=False)
+    flow = {"workload": FLOW["workload"], "m": int(F_np.shape[0]), "n": int(F_np.shape[1]), "k": FLOW["k"],
+            "c": FLOW["c"], "rounds": tf["rounds"], "ms_per_step": tf["ms"], "e2e_ms": tf["ms_e2e"],
+            "gpu_launches": int(tf["launches"])}
+    del F_np
+    cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, parts = oracle_sample(A_np, rounds)
-        cpu = {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": "FP64 NumPy/LAPACK oracle, column norms and refinement in full, %d of %d ISMA "
-                         "rounds timed and scaled to the whole problem" % (parts["rounds"], rounds)}
+        secs, ref = oracle_full(A_np, HEAD)
+        cpu = {"value": secs, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "the whole problem once: FP64 NumPy/LAPACK oracle (Algorithm 1, %d rounds, refinement) "
+                         "on the host cores" % len(ref.trace)}
+        acc = accuracy(t["U"], t["sigma"], ref, k)
+        acc["rounds_equal"] = int(len(ref.trace) == t["rounds"])
     if rank == 0:
-        line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        line = {"metric": METRIC, "value": t["ms"] / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t["ms"], "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "m": int(m), "n": int(n), "k": K_MODES, "c": C_DRAWS,
-                           "tol": TOL, "rounds": rounds, "strategy": "L2N round 0, UNF after",
+                "config": {"workload": HEAD["workload"], "m": int(m), "n": int(n), "k": k, "c": HEAD["c"],
+                           "tol": HEAD["tol"], "rounds": t["rounds"], "strategy": "L2N round 0, UNF after",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "contractions": "A^T U on tcgen05 tensor cores, split-TF32 (3 products)",
-                           "l2": "A is 0.80 GB, larger than the 129 MB L2: no flush between steps"},
-                "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(m * n * es),
-                        "d2h_bytes_per_step": int(m * K_MODES * 4 + K_MODES * 8)},
-                "gpu_launches": int(launches),
-                "core_svd": {"jacobi_sweeps_mean": float(np.mean(sweeps)) if sweeps else None,
-                             "jacobi_sweeps_max": int(np.max(sweeps)) if sweeps else None,
-                             "phase_cycles_mean": {k: round(v) for k, v in zip(
+                           "l2": "A is 16 GB, larger than the 129 MB L2: no flush between steps"},
+                "e2e": {"value": t["ms_e2e"] / 1e3, "unit": "s", "h2d_bytes_per_step": t["h2d"],
+                        "d2h_bytes_per_step": t["d2h"]},
+                "gpu_launches": int(t["launches"]),
+                "accuracy_vs_oracle": acc,
+                "core_svd": {"jacobi_sweeps_mean": float(np.mean(t["sweeps"])),
+                             "jacobi_sweeps_max": int(np.max(t["sweeps"])),
+                             "phase_cycles_mean": {kk: round(v) for kk, v in zip(
                                  ["chol2_and_E", "jacobi", "finish", "convergence", "coefficients", "total"],
                                  core_phase)}},
-                "roofline": roofline,
-                "clocks": clk,
+                "roofline": roof,
+                "flow_316": flow,
+                "clocks": t["clocks"],
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:

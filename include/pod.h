@@ -62,14 +62,22 @@ enum { POD_SUBSPACE = 0, POD_MODES = 1 };
 /* arithmetic of the core SVD of E (Algorithm 2):
  * POD_CORE_AUTO = FP64 for POD_F64 data, FP32 for POD_F32 data */
 enum { POD_CORE_AUTO = 0, POD_CORE_F32 = 1, POD_CORE_F64 = 2 };
-/* arithmetic of the dense contractions:
+/* arithmetic of the dense contractions U^T C (BLOCK MERGE's projection of
+ * the sampled columns, Algorithm 2) and A^T U (refinement, ORT weights):
  * POD_PREC_F32    FP32 SIMT products, FP64 sums of FP32 partials
- * POD_PREC_TF32X3 A^T U (refinement, ORT) on the tcgen05 tensor cores with
- *                 split-TF32 products (x = hi + lo, three TF32 products;
- *                 FP32-level accuracy), FP32 accumulation per 64 rows,
- *                 double-float across; FP32 data, m and lda multiples of 4,
- *                 r <= 64
- * POD_PREC_BF16, POD_PREC_BF16X3: not in this build (POD_EUNSUPPORTED) */
+ * POD_PREC_TF32X3 tcgen05 tensor cores, split-TF32 products (x = hi + lo
+ *                 exactly, three TF32 products hi hi + hi lo + lo hi):
+ *                 FP32-level products
+ * POD_PREC_BF16X3 tcgen05 tensor cores, split-BF16 products (x ~ b0 + b1,
+ *                 b0 = bf16(x), b1 = bf16(x - b0); b0 b0 + b0 b1 + b1 b0):
+ *                 about 2^-16 relative per product
+ * POD_PREC_BF16   tcgen05 tensor cores, one BF16 product: about 2^-8
+ * The tensor-core forms accumulate in FP32 over 64-row groups and in
+ * double-float / FP64 across groups; they need FP32 data, m and lda
+ * multiples of 4, 16-byte aligned A, r <= 64 (else POD_EUNSUPPORTED).  The
+ * residual's second projection (CGS2), the CholeskyQR Grams, the core SVD
+ * and the convergence test keep FP32 products with FP64-level sums, so the
+ * low-precision U^T C is corrected by the second projection. */
 enum { POD_PREC_F32 = 0, POD_PREC_BF16 = 1, POD_PREC_BF16X3 = 2, POD_PREC_TF32X3 = 3 };
 
 /*
@@ -101,9 +109,9 @@ typedef struct pod_params {
     int32_t block_trunc;   /* 1: GET UPDATE truncates the new block to rank r
                               through SVD(D^T D) before the merge (the paper's
                               literal Algorithm 1); 0: D merges directly     */
-    int32_t precision;     /* POD_PREC_F32 | POD_PREC_TF32X3 (see above);
-                              TF32X3 with an unsupported shape, and the BF16
-                              forms, are POD_EUNSUPPORTED                    */
+    int32_t precision;     /* POD_PREC_* (see above); a tensor-core form with
+                              FP64 data or an unsupported shape is
+                              POD_EUNSUPPORTED                               */
     int32_t keep_tape;     /* 1: record, per round, the basis U_t entering
                               the merge and the merge core (E, its singular
                               values and left vectors, Ptot, R^{-1}) so that
@@ -269,6 +277,20 @@ POD_API pod_status pod_reset(pod_ctx *ctx, const void *A_dev);
 POD_API pod_status pod_round_timings(pod_ctx *ctx, float *ms_host, int32_t cap, int32_t *count);
 
 /*
+ * pod_refine_timings -- run the closing refinement of Algorithm 1 (the step
+ * pod_modes runs first when p->refine is 1: Y = A^T U, CholeskyQR2 of Y,
+ * SVD(R), U <- U V_R) launch by launch with a CUDA event recorded after
+ * every kernel, and return each kernel's duration in milliseconds in launch
+ * order: state, A^T U, state, Gram of Y, first Cholesky, state, second
+ * CholeskyQR pass, SVD of R, state, U V_R.  A later pod_modes reuses the
+ * refinement.  Synchronises.
+ *   ms_host : capacity cap floats;  count : entries written.
+ * Errors: POD_EINVAL, POD_ESTATE (refine = 0, refinement already run, or a
+ * poisoned context), POD_ECUDA, POD_ETIMEOUT.
+ */
+POD_API pod_status pod_refine_timings(pod_ctx *ctx, float *ms_host, int32_t cap, int32_t *count);
+
+/*
  * pod_counters -- number of kernels this context has launched (graph
  * replays count every kernel node) and ISMA rounds completed as of the last
  * synchronisation.  Host-only, never synchronises.
@@ -327,9 +349,10 @@ POD_API pod_status pod_colnorms(const void *A_dev, int32_t dtype, int64_t m, int
  *   A_dev : device, m x n column-major (lda), dtype.
  *   U_dev : device, m x r column-major (ld m), dtype.
  *   Y_dev : device, n x r FP64 column-major (ld n), overwritten.
- *   precision : POD_PREC_F32 (FP32 SIMT / FP64 SIMT for FP64 data) or
- *               POD_PREC_TF32X3 (tcgen05, FP32 data, m and lda multiples of
- *               4, 16-byte aligned A and U, r <= 64; else POD_EUNSUPPORTED).
+ *   precision : POD_PREC_F32 (FP32 SIMT / FP64 SIMT for FP64 data) or a
+ *               tensor-core form POD_PREC_TF32X3 / BF16X3 / BF16 (FP32
+ *               data, m and lda multiples of 4, 16-byte aligned A and U,
+ *               r <= 64; else POD_EUNSUPPORTED).
  * Allocates its workspace for the call; synchronises the stream.
  * Errors: POD_EINVAL, POD_EUNSUPPORTED, POD_ENOMEM, POD_ECUDA, POD_ETIMEOUT.
  */

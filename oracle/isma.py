@@ -370,12 +370,17 @@ def refine(A: np.ndarray, U: np.ndarray):
     return U @ VRt.T, SR, Q @ UR
 
 
-def isma(A: np.ndarray, p: Params) -> Result:
-    """Algorithm 1 of the paper, in FP64, with the readings listed above."""
+def isma_steps(A: np.ndarray, p: Params):
+    """Algorithm 1 of the paper, in FP64, with the readings listed above, as a
+    generator that pauses after each unit of work: it yields ("norms", None)
+    once the column norms exist, ("round", t) after each round t, and finally
+    ("done", Result) after the refinement.  ``isma`` runs it to the end; the
+    pauses only let a caller time the units one by one."""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     r = p.carried_rank()
     s = column_sq_norms(A)
+    yield "norms", None
     in_S = np.ones(n, dtype=bool)
     U = np.zeros((m, 0))
     sig = np.zeros(0)
@@ -404,6 +409,7 @@ def isma(A: np.ndarray, p: Params) -> Result:
                 converged = True
             if p.criterion == "modes" and cos_min >= p.tol:
                 converged = True
+        yield "round", t
         t += 1
         if converged or not in_S.any() or t > p.max_iter:
             break
@@ -414,7 +420,15 @@ def isma(A: np.ndarray, p: Params) -> Result:
     sig_all = sig.copy()
     U, V = U[:, :kk], (V[:, :kk] if V is not None else None)
     U, V = fix_signs(U, V, p.seed)
-    return Result(U=U, sigma=sig[:kk], V=V, trace=trace, converged=converged, sigma_all=sig_all)
+    yield "done", Result(U=U, sigma=sig[:kk], V=V, trace=trace, converged=converged, sigma_all=sig_all)
+
+
+def isma(A: np.ndarray, p: Params) -> Result:
+    """Algorithm 1 of the paper, in FP64, with the readings listed above."""
+    for kind, val in isma_steps(A, p):
+        if kind == "done":
+            return val
+    raise AssertionError("unreachable")
 
 
 # ----------------------------------------------------------------------------

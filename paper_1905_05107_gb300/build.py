@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpod_gb300.so")
-SOURCES = ["sampler.cu", "tall.cu", "small.cu", "rows.cu", "wedin.cu", "atu_tc.cu", "backward.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["sampler.cu", "tall.cu", "small.cu", "rows.cu", "wedin.cu", "xty_tc.cu", "backward.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

@@ -142,10 +142,11 @@ struct pod_ctx {
     TapePtrs tape_h;
     TapePtrs *tape_d;
     bool modes_done;
-    // A^T U on tensor cores (precision POD_PREC_TF32X3)
-    int use_tc;
+    // tensor-core contractions (precision TF32X3, BF16X3, BF16): A^T U
+    // (local sums into Y) and the round's U^T C (deferred sums, ICS only)
+    int use_tc, use_tc_proj;
     uint32_t tc_spin;   // pipeline-wait bound of the tensor-core kernels (0: default)
-    AtuTcPlan tcplan;
+    XtyTcPlan tcplan, pplan;
     double *tc_part;
     unsigned *tc_counters;
     // host
@@ -207,7 +208,7 @@ static pod_status check_params(const pod_params *p) {
     if (p->block_trunc != 0 && p->block_trunc != 1) return POD_EINVAL;
     if (p->precision < POD_PREC_F32 || p->precision > POD_PREC_TF32X3) return POD_EINVAL;
     if (p->keep_tape != 0 && p->keep_tape != 1) return POD_EINVAL;
-    if (p->precision != POD_PREC_F32 && p->precision != POD_PREC_TF32X3) return POD_EUNSUPPORTED;
+    if (p->precision != POD_PREC_F32 && p->dtype != POD_F32) return POD_EUNSUPPORTED;
     if (p->keep_tape && (p->rows || p->block_trunc)) return POD_EUNSUPPORTED;
     if (p->reserved != 0) return POD_EINVAL;
     if (p->c > 256 || (p->r > 0 ? p->r : p->k) > 256) return POD_EUNSUPPORTED;
@@ -314,23 +315,25 @@ static pod_status tape_reserve(pod_ctx *c, int slots) {
     return POD_OK;
 }
 
-// Y = A^T U (n x r_cur of state st): split-TF32 tensor cores when the
-// context runs at POD_PREC_TF32X3, FP32 SIMT otherwise.
+// Y = A^T U (n x r_cur of state st): tensor cores (split TF32, split BF16 or
+// BF16 products) when the context runs at a tensor-core precision, FP32 SIMT
+// otherwise.
 template <typename T>
 static pod_status enqueue_atu(pod_ctx *c, const DevState *st, const uint8_t *mask, cudaStream_t s) {
     if (c->use_tc) {
-        AtuTcArgs ta{};
-        ta.m = c->p.m;
-        ta.n = c->p.n;
-        ta.lda = c->p.lda;
-        ta.rmax = c->rmax;
-        ta.st = st;
-        ta.part = c->tc_part;
-        ta.Y = c->Y;
-        ta.counters = c->tc_counters;
-        ta.err = &c->st->status;
-        ta.spin = c->tc_spin;
-        return launch_atu_tc(ta, c->tcplan, (const float *)c->A, (const float *)c->U, s);
+        XtyTcArgs xa{};
+        xa.m = c->p.m;
+        xa.ncols = c->p.n;
+        xa.st = st;
+        xa.ny_from_state = 1;
+        xa.part = c->tc_part;
+        xa.out = c->Y;
+        xa.ldo_y = c->p.n;
+        xa.ldo_x = 1;
+        xa.counters = c->tc_counters;
+        xa.err = &c->st->status;
+        xa.spin = c->tc_spin;
+        return launch_xty_tc(xa, c->tcplan, (const float *)c->A, c->p.lda, c->p.n, (const float *)c->U, c->rmax, s);
     }
     AtuArgs<T> aa{};
     aa.m = c->p.m;
@@ -488,14 +491,35 @@ static pod_status enqueue_round(pod_ctx *c) {
     sp.rows_rect = c->rmax;
     sp.st = c->st;
     ta.out = c->P;
-    POD_TRY(launch_tall<T>(TALL_PROJ, ta, c->plan, s));
-    mark(c);
+    if (c->use_tc_proj && !(c->p.rows || c->p.block_trunc)) {
+        // U^T C on the tensor cores, the sampled columns read in place
+        XtyTcArgs xa{};
+        xa.m = c->p.m;
+        xa.gather = 1;
+        xa.idx = c->idx;
+        xa.st = c->st;
+        xa.ny_from_state = 1;
+        xa.deferred = 1;
+        xa.part = c->part;
+        xa.part_stride = ta.part_stride;
+        xa.ldo_y = c->cmax;
+        xa.ldo_x = 1;
+        xa.err = &c->st->status;
+        xa.spin = c->tc_spin;
+        POD_TRY(launch_xty_tc(xa, c->pplan, (const float *)c->A, c->p.lda, c->p.n, (const float *)c->U, c->rmax, s));
+        mark(c);
+        sp.nparts = c->pplan.grid;
+    } else {
+        POD_TRY(launch_tall<T>(TALL_PROJ, ta, c->plan, s));
+        mark(c);
+    }
     sp.stride = ta.part_stride;
     sp.out = c->P;
     sp.rect = 1;
     sp.tri = 0;
     POD_TRY(launch_sum_parts(sp, c->cmax, s));
     mark(c);
+    sp.nparts = c->plan.grid;
     ta.part_stride = sPG;
     ta.out = c->PG;
     POD_TRY(launch_tall<T>(TALL_CGS, ta, c->plan, s));
@@ -618,9 +642,9 @@ static pod_status run_refine(pod_ctx *c) {
     }
     // Y = A^T U
     k_set_state<<<1, 32, 0, s>>>(c->aux + 0, r, 0, 0, 1, 1);
-    c->launches += 1;
+    mark(c);
     POD_TRY(enqueue_atu<T>(c, c->aux + 0, nullptr, s));
-    c->launches += 1;
+    mark(c);
     // G = Y^T Y, CholeskyQR2 on the n x r matrix Y (FP64 tall passes)
     TallPlan yplan = tall_plan(POD_F64, n, r, r, c->sms);
     TallArgs<double> ya{};
@@ -647,11 +671,11 @@ static pod_status run_refine(pod_ctx *c) {
         yplan.groups + 1 > 64 + c->plan.groups)
         return POD_EUNSUPPORTED;
     k_set_state<<<1, 32, 0, s>>>(c->aux + 1, r, r, 0, 1, 1);
-    c->launches += 1;
+    mark(c);
     ya.st = c->aux + 1;
     ya.out = c->rG;
     POD_TRY(launch_tall<double>(TALL_PROJ, ya, yplan, s));
-    c->launches += 1;
+    mark(c);
     RefineArgs ra{};
     ra.r = r;
     ra.dtype = c->p.dtype;
@@ -664,19 +688,19 @@ static pod_status run_refine(pod_ctx *c) {
     ra.K = c->rK;
     ra.gws = c->refine_gs;
     POD_TRY(launch_refine_chol(ra, s));
-    c->launches += 1;
+    mark(c);
     k_set_state<<<1, 32, 0, s>>>(c->aux + 2, 0, r, 0, 1, 1);
-    c->launches += 1;
+    mark(c);
     ya.st = c->aux + 2;
     ya.M1 = c->rM1;
     ya.out = c->rG2;
     POD_TRY(launch_tall<double>(TALL_QR2, ya, yplan, s));
-    c->launches += 1;
+    mark(c);
     POD_TRY(launch_refine_svd(ra, s));
-    c->launches += 1;
+    mark(c);
     // U <- U V_R (in place)
     k_set_state<<<1, 32, 0, s>>>(c->aux + 3, r, 0, r, 1, 1);
-    c->launches += 1;
+    mark(c);
     TallArgs<T> ua = tall_args<T>(c, c->part, 0);
     ua.st = c->aux + 3;
     ua.rmax = r;
@@ -688,7 +712,7 @@ static pod_status run_refine(pod_ctx *c) {
     ua.gscratch = uplan.wide ? c->tall_gs : nullptr;   // (r, cmax) needs no more than the round's plan
     ua.gstride = uplan.gstride;
     POD_TRY(launch_tall<T>(TALL_UPDATE, ua, uplan, s));
-    c->launches += 1;
+    mark(c);
     POD_CUDA_TRY(cudaMemcpyAsync(c->sigma, c->rsig, r * sizeof(double), cudaMemcpyDeviceToDevice, s));
     c->refined = true;
     c->refined_r = r;
@@ -952,13 +976,16 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     } else if (p->block_trunc) {
         c->gplan = row_gram_plan(p->dtype, p->m, c->cmax, c->sms);
     }
-    if (p->precision == POD_PREC_TF32X3) {
-        if (!atu_tc_supported(p->dtype, p->m, p->lda, c->rmax, A_dev, A_dev)) {
+    if (p->precision != POD_PREC_F32) {
+        if (!xty_tc_supported(p->dtype, p->m, p->lda, c->rmax, A_dev, A_dev)) {
             free(c);
             return POD_EUNSUPPORTED;
         }
         c->use_tc = 1;
-        c->tcplan = atu_tc_plan(p->m, p->n, c->rmax, c->sms);
+        c->tcplan = xty_tc_plan(p->precision, p->m, p->n, c->rmax, c->sms, 0);
+        c->pplan = xty_tc_plan(p->precision, p->m, c->cmax, c->rmax, c->sms, 1);
+        // the deferred partials use the round's partial buffer (plan.grid slots)
+        c->use_tc_proj = c->pplan.grid <= c->plan.grid;
     }
     if ((p->rows || p->block_trunc) && rows_small_smem(c->cmax) > 220 * 1024) {
         free(c);
@@ -1449,6 +1476,49 @@ pod_status pod_round_timings(pod_ctx *c, float *ms_host, int32_t cap, int32_t *c
     return st;
 }
 
+pod_status pod_refine_timings(pod_ctx *c, float *ms_host, int32_t cap, int32_t *count) {
+    if (!c || !ms_host || cap <= 0 || !count) return POD_EINVAL;
+    if (c->poisoned) return POD_ESTATE;
+    if (!c->p.refine || c->refined) return POD_ESTATE;
+    *count = 0;
+    pod_status st = read_state(c);
+    if (st != POD_OK) {
+        c->poisoned = true;
+        return st;
+    }
+    const int nev = 16;
+    cudaEvent_t ev[nev];
+    for (int i = 0; i < nev; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+            return POD_ECUDA;
+        }
+    c->prof_ev = ev;
+    c->prof_cap = nev;
+    c->prof_n = 1;
+    cudaEventRecord(ev[0], c->stream);
+    st = c->p.dtype == POD_F32 ? run_refine<float>(c) : run_refine<double>(c);
+    const int n = c->prof_n;
+    c->prof_ev = nullptr;
+    c->prof_cap = 0;
+    c->prof_n = 0;
+    if (st == POD_OK) st = read_state(c);
+    if (st == POD_OK) {
+        int k = 0;
+        for (int i = 1; i < n && k < cap; ++i, ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+            ms_host[k] = ms;
+        }
+        *count = k;
+    }
+    for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+    if (st == POD_OK && c->hstate->status != 0) st = (pod_status)c->hstate->status;
+    if (st != POD_OK) c->poisoned = true;
+    return st;
+}
+
 pod_status pod_core_stats(pod_ctx *c, int32_t *sweeps, int64_t *cycles) {
     if (!c) return POD_EINVAL;
     if (c->poisoned) return POD_ESTATE;
@@ -1500,9 +1570,9 @@ pod_status pod_atu(const void *A_dev, int32_t dtype, int64_t m, int64_t n, int64
                    double *Y_dev, int32_t precision, void *stream) {
     if (!A_dev || !U_dev || !Y_dev || m <= 0 || n <= 0 || lda < m || r <= 0) return POD_EINVAL;
     if (dtype != POD_F32 && dtype != POD_F64) return POD_EINVAL;
-    if (precision != POD_PREC_F32 && precision != POD_PREC_TF32X3) return POD_EUNSUPPORTED;
-    const bool tc = precision == POD_PREC_TF32X3;
-    if (tc && !atu_tc_supported(dtype, m, lda, r, A_dev, U_dev)) return POD_EUNSUPPORTED;
+    if (precision < POD_PREC_F32 || precision > POD_PREC_TF32X3) return POD_EINVAL;
+    const bool tc = precision != POD_PREC_F32;
+    if (tc && !xty_tc_supported(dtype, m, lda, r, A_dev, U_dev)) return POD_EUNSUPPORTED;
     if (!tc && r > 256) return POD_EUNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     const int sms = device_sms();
@@ -1510,11 +1580,11 @@ pod_status pod_atu(const void *A_dev, int32_t dtype, int64_t m, int64_t n, int64
     double *part = nullptr;
     unsigned *cnt = nullptr;
     pod_status st = dalloc(&stt, 1);
-    AtuTcPlan tp{};
+    XtyTcPlan tp{};
     AtuPlan ap{};
     size_t ncnt = 0;
     if (tc) {
-        tp = atu_tc_plan(m, n, r, sms);
+        tp = xty_tc_plan(precision, m, n, r, sms, 0);
         if (st == POD_OK) st = dalloc(&part, tp.part_doubles);
         ncnt = (size_t)tp.mtiles;
     } else {
@@ -1527,17 +1597,18 @@ pod_status pod_atu(const void *A_dev, int32_t dtype, int64_t m, int64_t n, int64
     if (st == POD_OK) {
         k_set_state<<<1, 32, 0, s>>>(stt, r, 0, 0, 0, 1);
         if (tc) {
-            AtuTcArgs ta{};
-            ta.m = m;
-            ta.n = n;
-            ta.lda = lda;
-            ta.rmax = r;
-            ta.st = stt;
-            ta.part = part;
-            ta.Y = Y_dev;
-            ta.counters = cnt;
-            ta.err = &stt->status;
-            st = launch_atu_tc(ta, tp, (const float *)A_dev, (const float *)U_dev, s);
+            XtyTcArgs xa{};
+            xa.m = m;
+            xa.ncols = n;
+            xa.st = stt;
+            xa.ny_from_state = 1;
+            xa.part = part;
+            xa.out = Y_dev;
+            xa.ldo_y = n;
+            xa.ldo_x = 1;
+            xa.counters = cnt;
+            xa.err = &stt->status;
+            st = launch_xty_tc(xa, tp, (const float *)A_dev, lda, n, (const float *)U_dev, r, s);
         } else if (dtype == POD_F32) {
             AtuArgs<float> aa{};
             aa.m = m;

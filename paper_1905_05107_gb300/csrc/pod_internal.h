@@ -191,25 +191,38 @@ template <typename T>
 pod_status launch_row_gram(const RowArgs<T> &a, cudaStream_t s);
 int row_blocks(int64_t m);
 
-// ---------------------------------------------------------------- atu_tc.cu
-// Y = A^T U on tcgen05 tensor cores with split-TF32 products (FP32 data).
-struct AtuTcArgs {
-    int64_t m, n, lda;
-    int rmax;
-    const DevState *st;     // r = st->r_cur
-    double *part;           // mtiles x splits x 128 x nt
-    double *Y;              // n x r, ld n
+// ----------------------------------------------------------------- xty_tc.cu
+// D = X^T Y on the tensor cores for FP32 data (see xty_tc.cu): the projection
+// U^T C of BLOCK MERGE (X gathered from A or dense) and A^T U.
+struct XtyTcArgs {
+    int64_t m;              // rows (the reduction)
+    int64_t ncols;          // X columns when not gathered
+    int gather;             // 1: X = columns idx[0 .. st->g) of the matrix X (ld ldx)
+    const int32_t *idx;
+    const float *X;         // set by launch_xty_tc
+    int64_t ldx;
+    const DevState *st;     // done flag; st->r_cur Y columns when ny_from_state; st->g
+    int ny_from_state, ny;
+    int mtiles, maxcover;   // set by launch_xty_tc from the plan
+    int deferred;           // 1: per-CTA slots part[b * part_stride + yc * ldo_y + xc], summed elsewhere
+    double *part;
+    int64_t part_stride;
+    double *out;            // local sums: out[yc * ldo_y + xc * ldo_x]
+    int64_t ldo_y, ldo_x;
     unsigned *counters;     // one per M-tile, zero between launches
     int *err;               // set to POD_ETIMEOUT when a bounded wait expires
     uint32_t spin;          // polls before a pipeline wait gives up (0: default)
 };
-struct AtuTcPlan {
-    int nt, mtiles, splits;
+struct XtyTcPlan {
+    int mode, nt, grid, mtiles, maxcover;
     size_t smem, part_doubles;
 };
-int atu_tc_supported(int dtype, int64_t m, int64_t lda, int rmax, const void *A, const void *U);
-AtuTcPlan atu_tc_plan(int64_t m, int64_t n, int rmax, int sms);
-pod_status launch_atu_tc(const AtuTcArgs &a, const AtuTcPlan &plan, const float *A, const float *U, cudaStream_t s);
+int xty_tc_mode_ok(int mode);
+int xty_tc_supported(int dtype, int64_t m, int64_t ldx, int ny_max, const void *X, const void *Y);
+XtyTcPlan xty_tc_plan(int mode, int64_t m, int64_t ncols_max, int ny_max, int sms, int deferred);
+pod_status launch_xty_tc(const XtyTcArgs &a, const XtyTcPlan &plan, const float *X, int64_t ldx, int64_t xcols,
+                         const float *Y, int64_t ycols, cudaStream_t s);
+
 
 // ------------------------------------------------------------------ wedin.cu
 // Eq. 7 residual norms after the refinement (see wedin.cu).

@@ -280,9 +280,15 @@ __device__ int jacobi_hw(J *B, int ldb, int nrow, int ncol, J *V, int ldv, J *al
 // finish needs).  V is rotated only when WITHV.  (Four lanes per pair
 // measured faster than 8 or 16 on 60-column cores, and 16-byte row groups
 // than 4-byte rows.)
-constexpr int LEAN_LD = 64;
+constexpr int LEAN_LD = 64;     // smallest leading dimension of the lean layout
+constexpr int LEAN_MAX = 160;   // widest core the lean layout serves
 
-template <bool WITHV>
+// leading dimension of the lean layout for cores up to nmax wide
+__host__ __device__ inline int lean_ld(int nmax) {
+    return nmax <= 64 ? 64 : (nmax <= 96 ? 96 : (nmax <= 128 ? 128 : 160));
+}
+
+template <bool WITHV, int LD>
 __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol, int max_sweeps, int *s_flag,
                            int keep_top = 0) {
     // keep_top > 0: only the keep_top rows of largest norm are used afterwards,
@@ -294,25 +300,30 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
     // go on over every pair.
     __shared__ float s_thr;
     constexpr int LP = 4, PPW = 8;
+    constexpr int KG = LD / 16;   // 16-row groups of a row; each lane holds one float4 of each
     const int N = ncol + (ncol & 1), npairs = N / 2, M = N - 1;
     const int nwork = 32 * ((npairs + PPW - 1) / PPW);
     const int tid = threadIdx.x;
     if (tid >= nwork) return 0;
     const int lane = tid & 31, lp = lane % LP, sub = lane / LP, pr = (tid >> 5) * PPW + sub;
     const bool active = pr < npairs;
-    int off[4];   // float4 index of row group k: rows 16 ((k + sub) mod 4) + 4 lp .. + 3
+    // float4 index of this lane's part of row group k: rows 16 ((k + sub) mod
+    // KG) + 4 lp .. + 3 (rows start on bank 0 since LD is a multiple of 32
+    // floats; the rotation by sub puts the two pairs of an 8-lane phase 16
+    // banks apart)
+    int off[KG];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) off[k] = 4 * ((k + sub) & 3) + lp;
+    for (int k = 0; k < KG; ++k) off[k] = 4 * ((k + sub) % KG) + lp;
     const float tol2 = tol * tol, loose = 16.f * tol, loose2 = loose * loose;
     const int max_sweeps0 = max_sweeps;
     int sweep = 0;
     for (;;) {   // a second pass only when the guard below turns the skipping off
     for (;; ++sweep) {
         for (int c = tid; c < ncol; c += nwork) {
-            const float4 *bc = reinterpret_cast<const float4 *>(B + (size_t)c * LEAN_LD);
+            const float4 *bc = reinterpret_cast<const float4 *>(B + (size_t)c * LD);
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-            for (int i = 0; i < LEAN_LD / 4; i += 2) {
+            for (int i = 0; i < LD / 4; i += 2) {
                 const float4 u0 = bc[i], u1 = bc[i + 1];
                 s0 = fmaf(u0.x, u0.x, fmaf(u0.y, u0.y, fmaf(u0.z, u0.z, fmaf(u0.w, u0.w, s0))));
                 s1 = fmaf(u1.x, u1.x, fmaf(u1.y, u1.y, fmaf(u1.z, u1.z, fmaf(u1.w, u1.w, s1))));
@@ -346,18 +357,18 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
         for (int rnd = 0; rnd < M; ++rnd) {
             const int p = active ? min(pa, qa) : 0, q = active ? max(pa, qa) : 0;
             const bool valid = active && q < ncol;
-            float4 *bp = reinterpret_cast<float4 *>(B + (size_t)p * LEAN_LD);
-            float4 *bq = reinterpret_cast<float4 *>(B + (size_t)(valid ? q : p) * LEAN_LD);
-            float4 x[4], y[4];
+            float4 *bp = reinterpret_cast<float4 *>(B + (size_t)p * LD);
+            float4 *bq = reinterpret_cast<float4 *>(B + (size_t)(valid ? q : p) * LD);
+            float4 x[KG], y[KG];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < KG; ++k) {
                 x[k] = bp[off[k]];
                 y[k] = bq[off[k]];
             }
             const float a = alpha[p], b = alpha[valid ? q : p];
             float g0 = 0.f, g1 = 0.f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < KG; ++k) {
                 g0 = fmaf(x[k].x, y[k].x, g0);
                 g1 = fmaf(x[k].y, y[k].y, g1);
                 g0 = fmaf(x[k].z, y[k].z, g0);
@@ -382,17 +393,17 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
                     const float sn = copysignf(1.f, d) * (0.5f * h) * (ir * iy);
                     const float t = sn * iy;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < KG; ++k) {
                         bp[off[k]] = make_float4(fmaf(cs, x[k].x, -sn * y[k].x), fmaf(cs, x[k].y, -sn * y[k].y),
                                                  fmaf(cs, x[k].z, -sn * y[k].z), fmaf(cs, x[k].w, -sn * y[k].w));
                         bq[off[k]] = make_float4(fmaf(sn, x[k].x, cs * y[k].x), fmaf(sn, x[k].y, cs * y[k].y),
                                                  fmaf(sn, x[k].z, cs * y[k].z), fmaf(sn, x[k].w, cs * y[k].w));
                     }
                     if (WITHV) {
-                        float4 *vp = reinterpret_cast<float4 *>(V + (size_t)p * LEAN_LD);
-                        float4 *vq = reinterpret_cast<float4 *>(V + (size_t)q * LEAN_LD);
+                        float4 *vp = reinterpret_cast<float4 *>(V + (size_t)p * LD);
+                        float4 *vq = reinterpret_cast<float4 *>(V + (size_t)q * LD);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
+                        for (int k = 0; k < KG; ++k) {
                             const float4 vx = vp[off[k]], vy = vq[off[k]];
                             vp[off[k]] = make_float4(fmaf(cs, vx.x, -sn * vy.x), fmaf(cs, vx.y, -sn * vy.y),
                                                      fmaf(cs, vx.z, -sn * vy.z), fmaf(cs, vx.w, -sn * vy.w));
@@ -422,9 +433,9 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
         if (!big) {
             ++sweep;
             for (int c = tid; c < ncol; c += nwork) {
-                const float *bc = B + (size_t)c * LEAN_LD;
+                const float *bc = B + (size_t)c * LD;
                 float s0 = 0.f;
-                for (int i = 0; i < LEAN_LD; ++i) s0 = fmaf(bc[i], bc[i], s0);
+                for (int i = 0; i < LD; ++i) s0 = fmaf(bc[i], bc[i], s0);
                 alpha[c] = s0;
             }
             break;
@@ -436,7 +447,7 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
     // |b_i . b_j|); if that reaches the keep_top-th largest alpha, the
     // sweeps go on over every pair
     if (keep_top > 0 && keep_top < ncol) {
-        __shared__ int s_top[LEAN_LD];
+        __shared__ int s_top[LD];
         __shared__ float s_amin;
         __shared__ int s_bad;
         bar_sync_1(nwork);   // the final norms are in
@@ -459,25 +470,25 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
         for (int e = tid; e < ncol * ncol; e += nwork) {
             const int i = e / ncol, j = e - i * ncol;
             if (i >= j || s_top[i] || s_top[j]) continue;
-            const float4 *bi = reinterpret_cast<const float4 *>(B + (size_t)i * LEAN_LD);
-            const float4 *bj = reinterpret_cast<const float4 *>(B + (size_t)j * LEAN_LD);
+            const float4 *bi = reinterpret_cast<const float4 *>(B + (size_t)i * LD);
+            const float4 *bj = reinterpret_cast<const float4 *>(B + (size_t)j * LD);
             float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-            for (int k = 0; k < LEAN_LD / 4; k += 2) {
+            for (int k = 0; k < LD / 4; k += 2) {
                 const float4 x0 = bi[k], y0 = bj[k], x1 = bi[k + 1], y1 = bj[k + 1];
                 d0 = fmaf(x0.x, y0.x, fmaf(x0.y, y0.y, fmaf(x0.z, y0.z, fmaf(x0.w, y0.w, d0))));
                 d1 = fmaf(x1.x, y1.x, fmaf(x1.y, y1.y, fmaf(x1.z, y1.z, fmaf(x1.w, y1.w, d1))));
             }
             const float d = fabsf(d0 + d1);
-            Dm[i * LEAN_LD + j] = d;
-            Dm[j * LEAN_LD + i] = d;
+            Dm[i * LD + j] = d;
+            Dm[j * LD + i] = d;
         }
         bar_sync_1(nwork);
         for (int i = tid; i < ncol; i += nwork) {
             if (s_top[i]) continue;
             float rad = 0.f;
             for (int j = 0; j < ncol; ++j)
-                if (j != i && !s_top[j]) rad += Dm[i * LEAN_LD + j];
+                if (j != i && !s_top[j]) rad += Dm[i * LD + j];
             if (alpha[i] + rad >= s_amin) s_bad = 1;
         }
         bar_sync_1(nwork);
@@ -595,36 +606,44 @@ __device__ double top_singular_value(J *B, int ld, int nrow, int k, J *M, J *alp
     int s = 0;
     for (int j = 0; j < smax; ++j) {
         const J *qj = Q + (size_t)j * k;
-        // w = M q_j
-        for (int i = grp; i < k; i += ngrp) {
+        // w = M q_j (the loops step by the CTA's group count from 0, so
+        // every lane of a warp runs the same iterations and takes part in
+        // every shuffle; groups past the end contribute zeros)
+        for (int i0 = 0; i0 < k; i0 += ngrp) {
+            const int i = i0 + grp;
             J v = 0;
-            for (int l = lane8; l < k; l += 8) v = fma(M[i * k + l], qj[l], v);
+            if (i < k)
+                for (int l = lane8; l < k; l += 8) v = fma(M[i * k + l], qj[l], v);
             v += __shfl_xor_sync(0xffffffffu, v, 4);
             v += __shfl_xor_sync(0xffffffffu, v, 2);
             v += __shfl_xor_sync(0xffffffffu, v, 1);
-            if (lane8 == 0) wv[i] = v;
+            if (i < k && lane8 == 0) wv[i] = v;
         }
         __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {
             J *c = cv + pass * (LZ_STEPS + 1);
             // c_l = q_l^T w, l <= j
-            for (int l = grp; l <= j; l += ngrp) {
+            for (int l0 = 0; l0 <= j; l0 += ngrp) {
+                const int l = l0 + grp;
                 J v = 0;
-                for (int i = lane8; i < k; i += 8) v = fma(Q[(size_t)l * k + i], wv[i], v);
+                if (l <= j)
+                    for (int i = lane8; i < k; i += 8) v = fma(Q[(size_t)l * k + i], wv[i], v);
                 v += __shfl_xor_sync(0xffffffffu, v, 4);
                 v += __shfl_xor_sync(0xffffffffu, v, 2);
                 v += __shfl_xor_sync(0xffffffffu, v, 1);
-                if (lane8 == 0) c[l] = v;
+                if (l <= j && lane8 == 0) c[l] = v;
             }
             __syncthreads();
             // w -= sum_l c_l q_l
-            for (int i = grp; i < k; i += ngrp) {
+            for (int i0 = 0; i0 < k; i0 += ngrp) {
+                const int i = i0 + grp;
                 J v = 0;
-                for (int l = lane8; l <= j; l += 8) v = fma(c[l], Q[(size_t)l * k + i], v);
+                if (i < k)
+                    for (int l = lane8; l <= j; l += 8) v = fma(c[l], Q[(size_t)l * k + i], v);
                 v += __shfl_xor_sync(0xffffffffu, v, 4);
                 v += __shfl_xor_sync(0xffffffffu, v, 2);
                 v += __shfl_xor_sync(0xffffffffu, v, 1);
-                if (lane8 == 0) wv[i] -= v;
+                if (i < k && lane8 == 0) wv[i] -= v;
             }
             __syncthreads();
         }
@@ -876,8 +895,9 @@ __host__ __device__ inline CoreLayout core_layout(int rmax, int cmax, int jsize)
     // FP32 path: 3 X + 8 float g x g arrays; FP64 path: 5 X arrays
     L.phaseA = jsize == 4 ? 3 * al16x((size_t)cmax * cmax * 8) + 8 * al16x((size_t)cmax * cmax * 4)
                           : 5 * al16x((size_t)cmax * cmax * 8);
-    // B, V: leading dimension 64 (zero-padded rows) on the lean FP32 path (n_c <= 64)
-    const size_t jb = (jsize == 4 && nmax <= LEAN_LD) ? (size_t)LEAN_LD * nmax : (size_t)nmax * nmax;
+    // B, V: leading dimension lean_ld(nmax) (zero-padded rows) on the lean
+    // FP32 path (n_c <= 160)
+    const size_t jb = (jsize == 4 && nmax <= LEAN_MAX) ? (size_t)lean_ld(nmax) * nmax : (size_t)nmax * nmax;
     L.phaseB = 2 * al16x(jb * jsize) + al16x((size_t)nmax * jsize) + al16x((size_t)nmax * 4);
     // Vr, Q, Yt: nmax x rmax X; Gb, Rb, Mw, Mb: rmax x rmax X; Bs: nmax x rmax J;
     // BtB: rmax^2 J; xv, yv: max(rmax, LZ_STEPS + 1) J; Lanczos work: rmax +
@@ -1150,10 +1170,10 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     // ---- phase B: Jacobi on the rows of E: B = E^T (column p = row p of E)
     // (wide cores: B, V in shared memory when they fit, else in global scratch)
     Carve cvB{(gbase && a.jac_smem) ? smem_raw : work};
-    const bool lean = sizeof(J) == 4 && nmax <= LEAN_LD;
-    const int ldj = lean ? LEAN_LD : nc;   // leading dimension of B and V
-    J *B = cvB.take<J>(lean ? (size_t)LEAN_LD * nmax : (size_t)nmax * nmax);
-    J *V = cvB.take<J>(lean ? (size_t)LEAN_LD * nmax : (size_t)nmax * nmax);
+    const bool lean = sizeof(J) == 4 && nmax <= LEAN_MAX;
+    const int ldj = lean ? lean_ld(nmax) : nc;   // leading dimension of B and V
+    J *B = cvB.take<J>(lean ? (size_t)ldj * nmax : (size_t)nmax * nmax);
+    J *V = cvB.take<J>(lean ? (size_t)ldj * nmax : (size_t)nmax * nmax);
     J *alpha = cvB.take<J>(nmax);
     int *order = cvB.take<int>(nmax);
     Carve cv = (gbase && a.jac_smem) ? Carve{work} : cvB;
@@ -1203,9 +1223,32 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     if (tid == 0) s_flag[1] = 0;
     int nsweeps;
     if constexpr (sizeof(J) == 4) {
-        if (lean && a.tape) nsweeps = jacobi_lean<true>(B, nc, V, alpha, tol, 20, s_flag);
-        else if (lean) nsweeps = jacobi_lean<false>(B, nc, V, alpha, tol, 20, s_flag, a.wq ? (a.r < nc ? a.r : nc) : 0);
-        else nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 20, s_flag);
+        if (lean) {
+            float *Bf = reinterpret_cast<float *>(B), *Vf = reinterpret_cast<float *>(V);
+            float *af = reinterpret_cast<float *>(alpha);
+            const float tf = (float)tol;
+            const int keep = a.wq ? (a.r < nc ? a.r : nc) : 0;
+            switch (ldj) {
+                case 64:
+                    nsweeps = a.tape ? jacobi_lean<true, 64>(Bf, nc, Vf, af, tf, 20, s_flag)
+                                     : jacobi_lean<false, 64>(Bf, nc, Vf, af, tf, 20, s_flag, keep);
+                    break;
+                case 96:
+                    nsweeps = a.tape ? jacobi_lean<true, 96>(Bf, nc, Vf, af, tf, 20, s_flag)
+                                     : jacobi_lean<false, 96>(Bf, nc, Vf, af, tf, 20, s_flag, keep);
+                    break;
+                case 128:
+                    nsweeps = a.tape ? jacobi_lean<true, 128>(Bf, nc, Vf, af, tf, 20, s_flag)
+                                     : jacobi_lean<false, 128>(Bf, nc, Vf, af, tf, 20, s_flag, keep);
+                    break;
+                default:
+                    nsweeps = a.tape ? jacobi_lean<true, 160>(Bf, nc, Vf, af, tf, 20, s_flag)
+                                     : jacobi_lean<false, 160>(Bf, nc, Vf, af, tf, 20, s_flag, keep);
+                    break;
+            }
+        } else {
+            nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 20, s_flag);
+        }
     } else {
         nsweeps = jacobi_hw<J>(B, nc, nc, nc, V, nc, alpha, tol, 30, s_flag);
     }

@@ -30,7 +30,8 @@ POD_PREC_F32, POD_PREC_BF16, POD_PREC_BF16X3, POD_PREC_TF32X3 = 0, 1, 2, 3
 EXPORTED = ["pod_init", "pod_iterate", "pod_modes", "pod_get_trace", "pod_replay_indices",
             "pod_backward", "pod_destroy", "pod_strerror", "pod_colnorms", "pod_sample",
             "pod_block_merge", "pod_reset", "pod_round_timings", "pod_counters", "pod_core_stats",
-            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental", "pod_robust_rounds", "pod_set_wait_limit"]
+            "pod_sample_noalloc", "pod_last_rows", "pod_row_draws", "pod_wedin", "pod_atu", "pod_incremental", "pod_robust_rounds", "pod_set_wait_limit",
+            "pod_refine_timings"]
 
 ROUND_KERNELS = ["sample", "proj", "proj_sum", "cgs_gram", "cgs_sum", "chol1", "qr2_gram", "qr2_sum", "cgs_robust",
                  "chol1_robust", "qr2_robust", "core_svd", "update"]
@@ -88,6 +89,7 @@ def lib():
         L.pod_core_stats.argtypes = [vp, P(i32), P(i64)]
         L.pod_sample_noalloc.argtypes = [vp, vp, i64, i32, u64, i32, i32, vp, vp, vp]
         L.pod_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
+        L.pod_refine_timings.argtypes = [vp, P(ctypes.c_float), i32, P(i32)]
         for name in EXPORTED:
             if name not in ("pod_destroy", "pod_strerror"):
                 getattr(L, name).restype = ctypes.c_int
@@ -246,6 +248,15 @@ class Context:
             (ORT_KERNELS if self.params.col_strategy == POD_ORT else []) + ROUND_KERNELS[:1] + \
             (ROW_KERNELS if self.params.rows else (ROW_KERNELS[1:] if self.params.block_trunc else [])) + \
             ROUND_KERNELS[1:]
+        return dict(zip(names, [float(x) for x in buf[: cnt.value]]))
+
+    def refine_timings(self):
+        """Runs the closing refinement with CUDA events between kernels;
+        returns {name: ms} (pod_refine_timings)."""
+        buf = (ctypes.c_float * 16)()
+        cnt = ctypes.c_int32(0)
+        _check(lib().pod_refine_timings(self._h, buf, 16, ctypes.byref(cnt)), "pod_refine_timings")
+        names = ["state0", "atu", "state1", "gram_y", "chol_y", "state2", "qr2_y", "svd_r", "state3", "update_u"]
         return dict(zip(names, [float(x) for x in buf[: cnt.value]]))
 
     def counters(self):
