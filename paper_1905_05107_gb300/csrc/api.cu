@@ -115,6 +115,7 @@ struct pod_ctx {
     double *part, *part_atu;
     double *P, *PG, *G2, *Ptot, *M1, *R1p, *E, *Xm, *Ym, *gsum;
     unsigned *counters, *atu_counters;
+    size_t part_cap, gsum_cap, counters_cap;   // doubles / doubles / counters allocated
     int vec;            // 16-byte copies legal for A and U
     double *rG, *rG2, *rM1, *rR1p, *rsig, *rVR, *rK, *dots, *part_sign;
     int32_t *replay_idx, *replay_off;
@@ -665,10 +666,8 @@ static pod_status run_refine(pod_ctx *c) {
     ya.gscratch = yplan.wide ? c->ytall_gs : nullptr;
     ya.gstride = yplan.gstride;
     if (yplan.wide && !c->ytall_gs) return POD_EUNSUPPORTED;
-    const size_t part_cap = (size_t)c->plan.grid * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax);
-    const size_t gsum_cap = (size_t)(c->plan.groups + 1) * ((size_t)c->rmax * c->cmax + (size_t)c->cmax * c->cmax);
-    if ((size_t)yplan.grid * r * r > part_cap || (size_t)(yplan.groups + 1) * r * r > gsum_cap ||
-        yplan.groups + 1 > 64 + c->plan.groups)
+    if ((size_t)yplan.grid * r * r > c->part_cap || (size_t)(yplan.groups + 1) * r * r > c->gsum_cap ||
+        (size_t)yplan.groups + 1 > c->counters_cap)
         return POD_EUNSUPPORTED;
     k_set_state<<<1, 32, 0, s>>>(c->aux + 1, r, r, 0, 1, 1);
     mark(c);
@@ -1032,11 +1031,21 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     ALLOC(c->hist_measure, n + 1);
     ALLOC(c->st, 1);
     ALLOC(c->aux, 6);
-    ALLOC(c->part, (size_t)c->plan.grid * ((size_t)rm * cm + (size_t)cm * cm));
+    {
+        // the round's tall passes and the refinement's Gram of Y = A^T U
+        // (n x r, FP64) share the partial buffers: size them for both
+        const TallPlan yp = tall_plan(POD_F64, n, rm, rm, c->sms);
+        c->part_cap = (size_t)c->plan.grid * ((size_t)rm * cm + (size_t)cm * cm);
+        if ((size_t)yp.grid * rm * rm > c->part_cap) c->part_cap = (size_t)yp.grid * rm * rm;
+        c->gsum_cap = (size_t)(c->plan.groups + 1) * ((size_t)rm * cm + (size_t)cm * cm);
+        if ((size_t)(yp.groups + 1) * rm * rm > c->gsum_cap) c->gsum_cap = (size_t)(yp.groups + 1) * rm * rm;
+        c->counters_cap = 64 + (c->plan.groups > yp.groups ? c->plan.groups : yp.groups);
+    }
+    ALLOC(c->part, c->part_cap);
     ALLOC(c->part_atu, (size_t)c->aplan.split * n * rm);
     ALLOC(c->P, (size_t)rm * cm);
-    ALLOC(c->gsum, (size_t)(c->plan.groups + 1) * ((size_t)rm * cm + (size_t)cm * cm));
-    ALLOC(c->counters, 64 + c->plan.groups);
+    ALLOC(c->gsum, c->gsum_cap);
+    ALLOC(c->counters, c->counters_cap);
     ALLOC(c->atu_counters, (size_t)c->aplan.grid.x + 64);
     ALLOC(c->PG, (size_t)rm * cm + (size_t)cm * cm);
     ALLOC(c->G2, (size_t)cm * cm);
@@ -1119,7 +1128,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (e == cudaSuccess) e = cudaMemsetAsync(c->P, 0, (size_t)rm * cm * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->PG, 0, ((size_t)rm * cm + (size_t)cm * cm) * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_g, 0, (n + 1) * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, (64 + c->plan.groups) * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, c->counters_cap * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->atu_counters, 0, (c->aplan.grid.x + 64) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sum_counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->upd_counter, 0, sizeof(unsigned), s);
