@@ -126,6 +126,20 @@ __global__ void __launch_bounds__(1024) k_sample(SampleArgs a) {
     const int t = st ? st->t : a.t_fixed;
     const int64_t n = a.n;
 
+    if (st && a.s) {
+        // a column norm that is not finite means a NaN or an infinity in A:
+        // the run stops with POD_ENAN before any merge uses the column
+        int bad = 0;
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) bad |= !isfinite(a.s[j]);
+        if (__syncthreads_or(bad)) {
+            if (threadIdx.x == 0) {
+                st->status = POD_ENAN;
+                st->done = 1;
+            }
+            return;
+        }
+    }
+
     if (a.replay_idx) {
         // frozen draws: round t merges replay list t
         if (t >= a.replay_T) {

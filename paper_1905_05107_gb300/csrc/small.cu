@@ -536,6 +536,11 @@ __device__ void sort_desc(const K *key, int n, int *order) {
 // Work arrays: M k^2, alpha and beta LZ_STEPS + 1 each, wv k, cv 2 (LZ_STEPS
 // + 1).  Called by the whole CTA; the result is valid in threads 0..31.
 constexpr int LZ_STEPS = 64;
+constexpr int LZ_WARP_K = 64;   // k up to this: the one-warp Lanczos
+constexpr int LZ_LDQ = 65;      // its leading dimension (odd: bank-disjoint)
+__host__ __device__ inline size_t lz_warp_words(int rmax) {
+    return rmax <= LZ_WARP_K ? (size_t)rmax * LZ_LDQ + LZ_WARP_K + 2 * LZ_LDQ : 0;
+}
 
 template <typename J>
 __device__ int sturm_below(const J *al, const J *be, int s, J x) {
@@ -570,7 +575,7 @@ __device__ int sturm_below(const J *al, const J *be, int s, J x) {
 
 template <typename J>
 __device__ double top_singular_value(J *B, int ld, int nrow, int k, J *M, J *alpha, J *beta, J *wv, J *cv,
-                                     double *red_d) {
+                                     J *lzq, double *red_d) {
     const int tid = threadIdx.x, bd = blockDim.x;
     const int lane8 = tid & 7, grp = tid >> 3, ngrp = bd >> 3;
     J *red = reinterpret_cast<J *>(red_d);
@@ -593,17 +598,67 @@ __device__ double top_singular_value(J *B, int ld, int nrow, int k, J *M, J *alp
     tr *= sc;
     __syncthreads();
     for (int e = tid; e < k * k; e += bd) M[e] *= sc;
-    J *Q = B;                           // Lanczos vectors, k apart
     const int smax = k < LZ_STEPS ? k : LZ_STEPS;
+    const J eps = sizeof(J) == 4 ? (J)1.2e-7 : (J)2.3e-16;
+    int s = 0;
     __syncthreads();
+    if (k <= LZ_WARP_K) {
+        // one warp, no CTA barriers: lane i holds rows i and i + 32 of each
+        // product; Lanczos vector l is column l of QT (k x LZ_LDQ, the odd
+        // leading dimension keeps a warp's accesses to distinct banks)
+        if (tid < 32) {
+            const int lane = tid;
+            J *QT = lzq, *w = lzq + (size_t)k * LZ_LDQ, *c0 = w + LZ_WARP_K;
+            J nrm0 = 0;
+            for (int i = 0; i < k; ++i) nrm0 += M[i * k + i];
+            const J inv0 = (J)1 / sqrt(nrm0);
+            for (int i = lane; i < k; i += 32) QT[i * LZ_LDQ] = sqrt(M[i * k + i]) * inv0;
+            __syncwarp();
+            for (int j = 0; j < smax; ++j) {
+                for (int i = lane; i < k; i += 32) {      // w = M q_j (M symmetric: read M[t][i])
+                    J v = 0;
+                    for (int t = 0; t < k; ++t) v = fma(M[t * k + i], QT[t * LZ_LDQ + j], v);
+                    w[i] = v;
+                }
+                __syncwarp();
+                for (int pass = 0; pass < 2; ++pass) {
+                    J *c = c0 + pass * LZ_LDQ;
+                    for (int l = lane; l <= j; l += 32) {   // c_l = q_l^T w
+                        J v = 0;
+                        for (int i = 0; i < k; ++i) v = fma(QT[i * LZ_LDQ + l], w[i], v);
+                        c[l] = v;
+                    }
+                    __syncwarp();
+                    for (int i = lane; i < k; i += 32) {    // w -= sum_l c_l q_l
+                        J v = 0;
+                        for (int l = 0; l <= j; ++l) v = fma(c[l], QT[i * LZ_LDQ + l], v);
+                        w[i] -= v;
+                    }
+                    __syncwarp();
+                }
+                J w2 = 0;
+                for (int i = lane; i < k; i += 32) w2 = fma(w[i], w[i], w2);
+                const J bnorm = sqrt(warp_sum(w2));
+                if (lane == 0) {
+                    alpha[j] = c0[j] + c0[LZ_LDQ + j];
+                    beta[j] = bnorm;
+                }
+                s = j + 1;
+                if (!(bnorm > (J)8 * eps * (J)k) || j + 1 == smax) break;
+                const J inv = (J)1 / bnorm;
+                for (int i = lane; i < k; i += 32) QT[i * LZ_LDQ + j + 1] = w[i] * inv;
+                __syncwarp();
+            }
+            __syncwarp();
+        }
+    } else {
+    J *Q = B;                           // Lanczos vectors, k apart
     // q_0 ~ sqrt(M_ii)
     J nrm0 = 0;
     for (int i = 0; i < k; ++i) nrm0 += M[i * k + i];   // sum of squares of sqrt(M_ii)
     const J inv0 = (J)1 / sqrt(nrm0);
     for (int i = tid; i < k; i += bd) Q[i] = sqrt(M[i * k + i]) * inv0;
     __syncthreads();
-    const J eps = sizeof(J) == 4 ? (J)1.2e-7 : (J)2.3e-16;
-    int s = 0;
     for (int j = 0; j < smax; ++j) {
         const J *qj = Q + (size_t)j * k;
         // w = M q_j (the loops step by the CTA's group count from 0, so
@@ -660,6 +715,7 @@ __device__ double top_singular_value(J *B, int ld, int nrow, int k, J *M, J *alp
         const J inv = (J)1 / bnorm;
         for (int i = tid; i < k; i += bd) Q[(size_t)(j + 1) * k + i] = wv[i] * inv;
         __syncthreads();
+    }
     }
     __syncthreads();
     double result = 0.0;
@@ -905,7 +961,8 @@ __host__ __device__ inline CoreLayout core_layout(int rmax, int cmax, int jsize)
     const size_t lzv = (size_t)(rmax > LZ_STEPS + 1 ? rmax : LZ_STEPS + 1);
     L.phaseC = 3 * al16x((size_t)nmax * rmax * 8) + 4 * al16x((size_t)rmax * rmax * 8) +
                al16x((size_t)nmax * rmax * jsize) + al16x((size_t)rmax * rmax * jsize) + 2 * al16x(lzv * jsize) +
-               al16x(((size_t)rmax + 2 * (LZ_STEPS + 1)) * jsize) + al16x((size_t)rmax * 8) + al16x((size_t)rmax * 4);
+               al16x(((size_t)rmax + 2 * (LZ_STEPS + 1) + lz_warp_words(rmax)) * jsize) + al16x((size_t)rmax * 8) +
+               al16x((size_t)rmax * 4);
     const size_t bc = L.phaseB + L.phaseC;
     L.total = L.keep + (L.phaseA > bc ? L.phaseA : bc) + 64;
     return L;
@@ -1188,7 +1245,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     J *BtB = cv.take<J>((size_t)a.rmax * a.rmax);
     J *xv = cv.take<J>(a.rmax > LZ_STEPS + 1 ? a.rmax : LZ_STEPS + 1);
     J *yv = cv.take<J>(a.rmax > LZ_STEPS + 1 ? a.rmax : LZ_STEPS + 1);
-    J *lzw = cv.take<J>((size_t)a.rmax + 2 * (LZ_STEPS + 1));
+    J *lzw = cv.take<J>((size_t)a.rmax + 2 * (LZ_STEPS + 1) + lz_warp_words(a.rmax));
     X *sig = cv.take<X>(a.rmax);
     int *ord2 = cv.take<int>(a.rmax);
     const bool f32 = sizeof(J) == 4;
@@ -1464,7 +1521,8 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
                 Bs[cidx * nr + p] = (J)XOps<X>::to(Q[cidx * nc + k + p]);
             }
             __syncthreads();
-            const double smax = top_singular_value<J>(Bs, nr, nr, k, BtB, xv, yv, lzw, lzw + a.rmax, red);
+            const double smax =
+                top_singular_value<J>(Bs, nr, nr, k, BtB, xv, yv, lzw, lzw + a.rmax, lzw + a.rmax + 2 * (LZ_STEPS + 1), red);
             if (tid == 0) {
                 s_sin = smax;
                 s_measure = smax;
