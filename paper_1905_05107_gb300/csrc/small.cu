@@ -615,24 +615,47 @@ __device__ double top_singular_value(J *B, int ld, int nrow, int k, J *M, J *alp
             for (int i = lane; i < k; i += 32) QT[i * LZ_LDQ] = sqrt(M[i * k + i]) * inv0;
             __syncwarp();
             for (int j = 0; j < smax; ++j) {
+                // four partial sums per product: the chains of dependent
+                // FMAs (and their shared-memory loads) overlap four ways
                 for (int i = lane; i < k; i += 32) {      // w = M q_j (M symmetric: read M[t][i])
-                    J v = 0;
-                    for (int t = 0; t < k; ++t) v = fma(M[t * k + i], QT[t * LZ_LDQ + j], v);
-                    w[i] = v;
+                    J v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+                    int t = 0;
+                    for (; t + 4 <= k; t += 4) {
+                        v0 = fma(M[t * k + i], QT[t * LZ_LDQ + j], v0);
+                        v1 = fma(M[(t + 1) * k + i], QT[(t + 1) * LZ_LDQ + j], v1);
+                        v2 = fma(M[(t + 2) * k + i], QT[(t + 2) * LZ_LDQ + j], v2);
+                        v3 = fma(M[(t + 3) * k + i], QT[(t + 3) * LZ_LDQ + j], v3);
+                    }
+                    for (; t < k; ++t) v0 = fma(M[t * k + i], QT[t * LZ_LDQ + j], v0);
+                    w[i] = (v0 + v1) + (v2 + v3);
                 }
                 __syncwarp();
                 for (int pass = 0; pass < 2; ++pass) {
                     J *c = c0 + pass * LZ_LDQ;
                     for (int l = lane; l <= j; l += 32) {   // c_l = q_l^T w
-                        J v = 0;
-                        for (int i = 0; i < k; ++i) v = fma(QT[i * LZ_LDQ + l], w[i], v);
-                        c[l] = v;
+                        J v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+                        int i = 0;
+                        for (; i + 4 <= k; i += 4) {
+                            v0 = fma(QT[i * LZ_LDQ + l], w[i], v0);
+                            v1 = fma(QT[(i + 1) * LZ_LDQ + l], w[i + 1], v1);
+                            v2 = fma(QT[(i + 2) * LZ_LDQ + l], w[i + 2], v2);
+                            v3 = fma(QT[(i + 3) * LZ_LDQ + l], w[i + 3], v3);
+                        }
+                        for (; i < k; ++i) v0 = fma(QT[i * LZ_LDQ + l], w[i], v0);
+                        c[l] = (v0 + v1) + (v2 + v3);
                     }
                     __syncwarp();
                     for (int i = lane; i < k; i += 32) {    // w -= sum_l c_l q_l
-                        J v = 0;
-                        for (int l = 0; l <= j; ++l) v = fma(c[l], QT[i * LZ_LDQ + l], v);
-                        w[i] -= v;
+                        J v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+                        int l = 0;
+                        for (; l + 4 <= j + 1; l += 4) {
+                            v0 = fma(c[l], QT[i * LZ_LDQ + l], v0);
+                            v1 = fma(c[l + 1], QT[i * LZ_LDQ + l + 1], v1);
+                            v2 = fma(c[l + 2], QT[i * LZ_LDQ + l + 2], v2);
+                            v3 = fma(c[l + 3], QT[i * LZ_LDQ + l + 3], v3);
+                        }
+                        for (; l <= j; ++l) v0 = fma(c[l], QT[i * LZ_LDQ + l], v0);
+                        w[i] -= (v0 + v1) + (v2 + v3);
                     }
                     __syncwarp();
                 }

@@ -24,7 +24,7 @@
 // the same number of slabs whatever the tile count.  A range that crosses an
 // M-tile boundary yields one partial per M-tile it touches.
 //
-// CTA roles (384 threads):
+// CTA roles (512 threads):
 //   warp 0      producer: TMA copies of each slab into a ring, 128-byte
 //               swizzled (the layout the MMA descriptors read): X as one box
 //               of 128 columns (dense) or one 32-row box per sampled column
@@ -35,10 +35,12 @@
 //               64-row group, hand the accumulator to the epilogue
 //   warps 4-7   split (TF32: in place, hi and a lo copy) or convert (BF16:
 //               from the raw FP32 ring into a bf16 ring) each landed slab
-//   warps 8-11  drain each group's accumulator into double-float registers,
-//               write the CTA's FP64 partials; the last CTA of an M-tile sums
-//               the partials of that tile in a fixed order (or, deferred, the
-//               partials are left to a separate summing kernel)
+//   warps 8-15  drain each group's accumulator into double-float registers
+//               (two warps per TMEM lane quadrant, half of the columns each,
+//               so that the running sums stay in registers), write the CTA's
+//               FP64 partials; the last CTA of an M-tile sums the partials of
+//               that tile in a fixed order (or, deferred, the partials are
+//               left to a separate summing kernel)
 // Every pipeline wait is bounded: on expiry the CTA records POD_ETIMEOUT,
 // stops issuing work, waits (with the default bound) for its own copies and
 // MMAs, frees TMEM and returns.
@@ -49,7 +51,7 @@
 
 namespace {
 
-constexpr int XT_THREADS = 384;
+constexpr int XT_THREADS = 512;
 constexpr int XT_TM = 128;                   // X columns per M-tile
 constexpr uint32_t XT_SPIN = 1u << 24;       // default bound of a wait: try_wait polls
 constexpr int XT_SMEM_BUDGET = 200 * 1024;   // ring bytes per CTA
@@ -154,6 +156,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 TMEM columns of this warp's 32 lanes -> 16 registers per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
 
 // Ring layout of one (MODE, NT).  TF32: one ring, each stage holds the FP32
@@ -244,7 +260,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&drained[b], 128);
+            mbar_init(&drained[b], 256);
         }
         mbar_init(done, 1);
         s_abort = 0;
@@ -441,11 +457,13 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         }
     } else if (warp >= 8) {
         // ------------------------------------------------ epilogue
-        const int q = warp - 8;                    // TMEM lane quadrant
+        constexpr int NH = NT / 2;                 // columns per epilogue warp
+        const int q = warp & 3;                    // TMEM lane quadrant (warp % 4)
+        const int c0 = ((warp - 8) >> 2) * NH;     // this warp's first column
         const int row = q * 32 + lane;             // row of the M-tile
-        float ahi[NT], alo[NT];
+        float ahi[NH], alo[NH];
 #pragma unroll
-        for (int c = 0; c < NT; ++c) ahi[c] = alo[c] = 0.f;
+        for (int c = 0; c < NH; ++c) ahi[c] = alo[c] = 0.f;
         int gi = -1;
         for (int kc = 0; kc < nit; ++kc) {
             if (!group_start(kc)) continue;
@@ -455,16 +473,15 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[b], (gi >> 1) & 1, &s_abort, lim));
             if (!ok) break;
             tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT + c0);
+            float v[NH];
+            if constexpr (NH == 32) tmem_ld32(ta, v);
+            else tmem_ld16(ta, v);
 #pragma unroll
-            for (int c0 = 0; c0 < NT; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT + c0), v);
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const dfloat t2 = df_two_sum(ahi[c0 + c], v[c]);
-                    ahi[c0 + c] = t2.hi;
-                    alo[c0 + c] += t2.lo;
-                }
+            for (int c = 0; c < NH; ++c) {
+                const dfloat t2 = df_two_sum(ahi[c], v[c]);
+                ahi[c] = t2.hi;
+                alo[c] += t2.lo;
             }
             tc_fence_before();
             mbar_arrive(&drained[b]);
@@ -478,16 +495,16 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             if (a.deferred) {
                 double *slot = a.part + (int64_t)blockIdx.x * a.part_stride;
 #pragma unroll
-                for (int c = 0; c < NT; ++c)
-                    if (c < ny && xc < ncols) slot[(int64_t)c * a.ldo_y + xc] = (double)ahi[c] + (double)alo[c];
+                for (int c = 0; c < NH; ++c)
+                    if (c0 + c < ny && xc < ncols) slot[(int64_t)(c0 + c) * a.ldo_y + xc] = (double)ahi[c] + (double)alo[c];
             } else {
                 const int64_t bf = item_owner((int64_t)mt * nslab, W, G);
                 double *part = a.part + ((int64_t)mt * a.maxcover + (blockIdx.x - bf)) * (XT_TM * NT);
 #pragma unroll
-                for (int c = 0; c < NT; ++c) part[(size_t)c * XT_TM + row] = (double)ahi[c] + (double)alo[c];
+                for (int c = 0; c < NH; ++c) part[(size_t)(c0 + c) * XT_TM + row] = (double)ahi[c] + (double)alo[c];
             }
 #pragma unroll
-            for (int c = 0; c < NT; ++c) ahi[c] = alo[c] = 0.f;
+            for (int c = 0; c < NH; ++c) ahi[c] = alo[c] = 0.f;
         }
         // every epilogue warp runs what follows the same way, aborted or not
         const int mt0 = mt_of(0), mt1 = mt_of(nit - 1);
@@ -498,7 +515,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             for (int omt = 0; omt < a.mtiles; ++omt) {
                 if (omt >= mt0 && omt <= mt1) continue;
                 const int64_t oc = (int64_t)omt * XT_TM + row;
-                for (int c = 0; c < NT && c < ny; ++c)
+                for (int c = c0; c < c0 + NH && c < ny; ++c)
                     if (oc < ncols) slot[(int64_t)c * a.ldo_y + oc] = 0.0;
             }
         } else {
@@ -506,14 +523,14 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                 const int64_t bf = item_owner((int64_t)mt * nslab, W, G);
                 const int64_t bl = item_owner((int64_t)mt * nslab + nslab - 1, W, G);
                 __threadfence();
-                bar_named(1, 128);
+                bar_named(1, 256);
                 if (tid == 256) s_last = atomicAdd(&a.counters[mt], 1u) == (unsigned)(bl - bf);
-                bar_named(1, 128);
+                bar_named(1, 256);
                 if (s_last) {
                     __threadfence();
                     const int64_t xc = (int64_t)mt * XT_TM + row;
                     const double *pt = a.part + (int64_t)mt * a.maxcover * (XT_TM * NT);
-                    for (int c = 0; c < ny && c < NT; ++c) {
+                    for (int c = c0; c < c0 + NH && c < ny; ++c) {
                         double sum = 0.0;
                         for (int p = 0; p <= (int)(bl - bf); ++p)
                             sum += __ldcg(pt + (size_t)p * (XT_TM * NT) + (size_t)c * XT_TM + row);
@@ -521,7 +538,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     }
                     if (tid == 256) a.counters[mt] = 0;
                 }
-                bar_named(1, 128);   // s_last is reused for the next tile
+                bar_named(1, 256);   // s_last is reused for the next tile
             }
         }
     }
