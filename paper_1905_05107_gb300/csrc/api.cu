@@ -252,7 +252,6 @@ static TallArgs<T> tall_args(pod_ctx *c, double *part, int64_t stride) {
     a.Ym = c->Ym;
     a.gscratch = c->plan.wide ? c->tall_gs : nullptr;
     a.gstride = c->plan.gstride;
-    a.s_smem = c->plan.s_smem;
     return a;
 }
 
@@ -666,7 +665,6 @@ static pod_status run_refine(pod_ctx *c) {
     ya.vec = (n % 2) == 0;
     ya.gscratch = yplan.wide ? c->ytall_gs : nullptr;
     ya.gstride = yplan.gstride;
-    ya.s_smem = yplan.s_smem;
     if (yplan.wide && !c->ytall_gs) return POD_EUNSUPPORTED;
     if ((size_t)yplan.grid * r * r > c->part_cap || (size_t)(yplan.groups + 1) * r * r > c->gsum_cap ||
         (size_t)yplan.groups + 1 > c->counters_cap)
@@ -712,9 +710,6 @@ static pod_status run_refine(pod_ctx *c) {
     ua.bm = uplan.bm;
     ua.gscratch = uplan.wide ? c->tall_gs : nullptr;   // (r, cmax) needs no more than the round's plan
     ua.gstride = uplan.gstride;
-    ua.s_smem = uplan.s_smem;
-    if (uplan.wide && (!c->tall_gs || uplan.gstride > c->plan.gstride || uplan.grid > c->plan.grid))
-        return POD_EUNSUPPORTED;
     POD_TRY(launch_tall<T>(TALL_UPDATE, ua, uplan, s));
     mark(c);
     POD_CUDA_TRY(cudaMemcpyAsync(c->sigma, c->rsig, r * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -66,8 +66,6 @@ struct TallArgs {
     const double *Ym;       // g x rn, ld rmax
     unsigned char *gscratch;   // wide plans: per-CTA slices of gstride bytes (else null)
     int64_t gstride;
-    int s_smem;             // wide plans: coefficient tiles in shared memory, only the
-                            // accumulators in the scratch slice
     int cond;               // 1: run only when st->robust is set (and then with a
                             // compensated Gram in the CGS pass); the QR2 pass with
                             // cond = 0 sets st->robust from its G2
@@ -105,9 +103,7 @@ struct TallPlan {
     int bm;
     int groups;
     size_t smem;
-    int wide;               // FP64 accumulators (and, unless s_smem, the coefficient
-                            // tiles) in global scratch
-    int s_smem;             // wide plans: the coefficient tiles stay in shared memory
+    int wide;               // coefficient tiles and FP64 accumulators in global scratch
     int64_t gstride;        // bytes of scratch per CTA (wide plans)
 };
 

@@ -364,14 +364,6 @@ template <typename T>
 __host__ __device__ inline size_t gscratch_bytes(const SmemPlan &p) {
     return (((p.s1 + p.s2 + p.s3) * sizeof(T) + 15) / 16) * 16 + (p.acc1 + p.acc2) * 8;
 }
-// Semi-wide plans: slabs, coefficient tiles and the reduction tile in shared
-// memory (the row-space products then read every operand from shared
-// memory), only the FP64 accumulators in the scratch slice.
-template <typename T>
-__host__ __device__ inline size_t smem_bytes_semi(const SmemPlan &p) {
-    return (2 * p.buf + p.ws + p.s1 + p.s2 + p.s3) * sizeof(T) + (size_t)TALL_THREADS * 16 * sizeof(T) + 64;
-}
-__host__ __device__ inline size_t gscratch_bytes_semi(const SmemPlan &p) { return (p.acc1 + p.acc2) * 8; }
 
 // The second CholeskyQR Gram must be near I on its kept indices; if not, the
 // first pass lost accuracy (an ill-conditioned residual block): flag the
@@ -501,15 +493,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     T *Ws = buf1 + L.buf;
     T *S1, *S2, *S3, *red;
     double *acc1, *acc2;
-    if (a.gscratch && a.s_smem) {
-        unsigned char *gs = a.gscratch + (int64_t)blockIdx.x * a.gstride;
-        S1 = Ws + L.ws;
-        S2 = S1 + L.s1;
-        S3 = S2 + L.s2;
-        red = S3 + L.s3;
-        acc1 = reinterpret_cast<double *>(gs);
-        acc2 = acc1 + L.acc1;
-    } else if (a.gscratch) {
+    if (a.gscratch) {
         unsigned char *gs = a.gscratch + (int64_t)blockIdx.x * a.gstride;
         S1 = reinterpret_cast<T *>(gs);
         S2 = S1 + L.s1;
@@ -866,31 +850,7 @@ TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
         p.bm = bm;
         p.smem = bytes_for(bm);
     } else {
-        // semi-wide: only the FP64 accumulators in global scratch (the
-        // coefficient tiles stay in shared memory); else wide: coefficient
-        // tiles and accumulators in global scratch
-        auto semi_for = [&](int b) {
-            SmemPlan L = smem_plan(rmax, cmax, b);
-            return f32 ? smem_bytes_semi<float>(L) : smem_bytes_semi<double>(L);
-        };
-        for (int b = 64; b >= 32 && !bm; b >>= 1)
-            if (semi_for(b) <= 200 * 1024) bm = b;
-        if (bm) {
-            SmemPlan L = smem_plan(rmax, cmax, bm);
-            per_sm = 1;
-            p.bm = bm;
-            p.smem = semi_for(bm);
-            p.wide = 1;
-            p.s_smem = 1;
-            p.gstride = (int64_t)gscratch_bytes_semi(L);
-            const int64_t slabs_s = (m + bm - 1) / bm;
-            int64_t grid_s = (int64_t)num_sms;
-            if (grid_s > slabs_s) grid_s = slabs_s;
-            if (grid_s < 1) grid_s = 1;
-            p.grid = (int)grid_s;
-            p.groups = (p.grid + RED_GROUP - 1) / RED_GROUP;
-            return p;
-        }
+        // wide: coefficient tiles and accumulators in global scratch
         auto wide_for = [&](int b) {
             SmemPlan L = smem_plan(rmax, cmax, b);
             return f32 ? smem_bytes_wide<float>(L) : smem_bytes_wide<double>(L);
