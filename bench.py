@@ -398,9 +398,12 @@ def time_problem(torch, pod, A_np, w, steps, warmup, dev, world, detail):
     return out
 
 
-def roofline_of(t, m, n, k, hbm, bf16):
-    """The dominant kernel's roofline plus the streaming and tensor-core
-    kernels' fractions, from the per-kernel timings of one run."""
+def roofline_of(t, m, n, k, hbm, bf16, tc_proj):
+    """The dominant kernel's roofline plus every kernel's fractions, from the
+    per-kernel timings of one run.  The round's FP32 SIMT passes are bound by
+    whichever of HBM bytes and FP32 flops they are closer to; the tensor-core
+    contractions by HBM bytes (their split products keep the tensor pipe far
+    from busy), with the tensor-pipe fraction beside it."""
     per, rg, sweeps = t["per"], t["rg"], t["sweeps"]
     es = 4
     totals = {kname: float(np.sum(v)) for kname, v in per.items()}
@@ -410,21 +413,25 @@ def roofline_of(t, m, n, k, hbm, bf16):
         mdl = kernel_model(m, es, 0 if i == 0 else k, g)
         for kname in ("proj", "cgs_gram", "qr2_gram", "update"):
             moved[kname] = moved.get(kname, 0.0) + mdl[kname][0]
-            flops[kname] = flops.get(kname, 0.0) + mdl[kname][1]
+            flops[kname] = flops.get(kname, 0.0) + mdl[kname][1] * (3 if (kname == "proj" and tc_proj) else 1)
     moved["colnorms"] = float(m * n * es + n * 8)
+    flops["colnorms"] = 2.0 * m * n
     moved["refine_atu"] = float(m * n * es + m * k * es)
-    hbm_kernels = {}
-    for kname, b in moved.items():
+    flops["refine_atu"] = 3 * 2.0 * m * n * k
+    tf32_peak = bf16 * TF32_PER_BF16
+    tensor = {"proj"} if tc_proj else set()
+    tensor.add("refine_atu")
+    kernels = {}
+    for kname in moved:
         if kname not in totals or totals[kname] <= 0:
             continue
-        gbs = b / (totals[kname] * 1e-3) / 1e9
-        hbm_kernels[kname] = {"GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4)}
-    # tensor pipe of the refinement's A^T U: 3 split-TF32 products of 2 m n k
-    tf32_peak = bf16 * TF32_PER_BF16
-    atu_tflops = 3 * 2.0 * m * n * k / (totals["refine_atu"] * 1e-3) / 1e12
-    tensor = {"refine_atu": {"TFLOP/s": round(atu_tflops, 1), "peak": round(tf32_peak, 1),
-                             "frac": round(atu_tflops / tf32_peak, 4),
-                             "note": "split TF32 (3 products); peak = BF16 peak x nominal TF32/BF16 ratio"}}
+        sec = totals[kname] * 1e-3
+        gbs = moved[kname] / sec / 1e9
+        tfs = flops[kname] / sec / 1e12
+        peak_f = tf32_peak if kname in tensor else FP32_PEAK_TFLOPS
+        kernels[kname] = {"GB/s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4), "TFLOP/s": round(tfs, 2),
+                          "flop_frac": round(tfs / peak_f, 4),
+                          "flop_peak": "TF32 tensor" if kname in tensor else "FP32 SIMT"}
     core_flops = 0.0
     for i, g in enumerate(rg):
         nc = (0 if i == 0 else k) + g
@@ -440,25 +447,37 @@ def roofline_of(t, m, n, k, hbm, bf16):
                 "note": "one CTA on one of 152 SMs, latency-bound Jacobi rounds; frac of that SM's "
                         "FP32 peak: %.4f" % (achieved * 1e3 / FP32_SM_PEAK_GFLOPS)}
     else:
-        roof_kernel = dominant if dominant in moved else max((kk for kk in totals if kk in moved), key=totals.get)
-        launches_k = len(per[roof_kernel])
-        avg_ms = totals[roof_kernel] / launches_k
-        bytes_ = moved[roof_kernel] / launches_k
-        achieved = bytes_ / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": roof_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": ncu_traffic(roof_kernel),
-                "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms}
-    roof["time_share"] = {kk: round(totals[kk] / sum(totals.values()), 4) for kk in totals}
+        kk = dominant if dominant in kernels else max((x for x in totals if x in kernels), key=totals.get)
+        launches_k = len(per[kk])
+        avg_ms = totals[kk] / launches_k
+        kr = kernels[kk]
+        if kk not in tensor and kr["flop_frac"] > kr["hbm_frac"]:
+            roof = {"bound": "alu", "kernel": kk, "achieved": flops[kk] / launches_k / (avg_ms * 1e-3) / 1e12,
+                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": ncu_traffic(kk),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (FP32 FMA)",
+                    "algorithmic_flops_per_launch": flops[kk] / launches_k, "avg_launch_ms": avg_ms,
+                    "hbm_frac": kr["hbm_frac"]}
+        else:
+            roof = {"bound": "hbm", "kernel": kk, "achieved": moved[kk] / launches_k / (avg_ms * 1e-3) / 1e9,
+                    "peak": hbm, "unit": "GB/s", "traffic": ncu_traffic(kk),
+                    "algorithmic_bytes_per_launch": moved[kk] / launches_k, "avg_launch_ms": avg_ms}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["time_share"] = {x: round(totals[x] / sum(totals.values()), 4) for x in totals}
     roof["dominant_kernel"] = dominant
-    roof["hbm_kernels"] = hbm_kernels
-    roof["tensor_kernels"] = tensor
+    roof["kernels"] = kernels
     return roof
+
+
+def sin_max(U, W):
+    """Largest sine of the principal angles between span(U) and span(W)
+    (orthonormal columns): |(I - U U^T) W|_2."""
+    return float(np.linalg.norm(W - U @ (U.T @ W), 2))
 
 
 def accuracy(U, sigma, ref, k):
     """sigma relative errors and sin(theta) of the top-j subspaces against the
-    oracle, with the FP32 floor u sigma_1 / gap_j of the oracle's spectrum."""
-    from oracle import isma as O
+    oracle's result, with the FP32 floor u sigma_1 / gap_j of the oracle's
+    spectrum."""
     u32 = 5.96e-8
     rel = np.abs(sigma - ref.sigma) / ref.sigma
     sall = ref.sigma_all if ref.sigma_all is not None else ref.sigma
@@ -466,10 +485,99 @@ def accuracy(U, sigma, ref, k):
     for j in sorted({10, 20, 30, 40, k}):
         if j > k:
             continue
-        out["sin_top%d" % j] = float(O.sin_principal_max(ref.U[:, :j], U[:, :j]))
+        out["sin_top%d" % j] = sin_max(ref.U[:, :j], U[:, :j])
         out["floor_top%d" % j] = floor_u(sall, j, u32)
     out["sigma_rel_top20"] = float(rel[:20].max())
     return out
+
+
+def precision_forms(torch, pod, A_np, w, dev, steps=3):
+    """The same workload with U^T C and A^T U in split BF16 and in BF16 on
+    the tensor cores (and split TF32, the headline's form, for the same-run
+    comparison): device time per problem and the modes for the accuracy
+    report."""
+    A = torch.from_numpy(np.ascontiguousarray(A_np.T)).to(dev).t()
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        for prec in ("tf32x3", "bf16x3", "bf16"):
+            ctx = pod.Context(A, w["k"], w["c"], tol=w["tol"], stream=stream, precision=prec)
+
+            def step():
+                ctx.reset()
+                ctx.iterate()
+                return ctx.modes()
+
+            step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                U, sigma, _ = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[prec] = {"ms_per_step": e0.elapsed_time(e1) / steps, "rounds": ctx.counters()[1],
+                         "U": U.double().cpu().numpy(), "sigma": sigma.cpu().numpy()}
+            ctx.close()
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
+def differentiable_form(torch, pod, dev, reps=3):
+    """The differentiation workload (planted 200000 x 1000 FP32, k = 16,
+    c = 32; loss sum_i w_i (u_i^T g)^2): the plain forward, the forward that
+    records the tape, and pod_backward, device times; the taped forward's
+    modes against the plain forward's (equal subspace accuracy)."""
+    from paper_1905_05107_gb300 import synth
+    A_np = synth.make_diff_c4()
+    A = torch.from_numpy(np.ascontiguousarray(A_np.T)).to(dev).t()
+    wv, gv = synth.diff_loss_weights(16, A_np.shape[0])
+    stream = torch.cuda.Stream(dev)
+    res = {"workload": "planted-200000x1000-f32-diff", "k": 16, "c": 32}
+    with torch.cuda.stream(stream):
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps, out
+
+        plain = pod.Context(A, 16, 32, tol=1e-8, stream=stream)
+
+        def fwd_plain():
+            plain.reset()
+            plain.iterate()
+            return plain.modes()
+
+        res["forward_ms"], (U0, s0, _) = timed(fwd_plain)
+        plain.close()
+        gt = torch.as_tensor(gv, dtype=torch.float32, device=dev)
+        wt = torch.as_tensor(wv, dtype=torch.float64, device=dev)
+
+        def fwd_tape():
+            ctx = pod.Context(A, 16, 32, tol=1e-8, stream=stream, keep_tape=True)
+            ctx.iterate()
+            U, s, _ = ctx.modes()
+            return ctx, U, s
+
+        ms, (ctx, U1, s1) = timed(lambda: fwd_tape())
+        res["forward_tape_ms"] = ms
+        proj = U1.t().double() @ gt.double()
+        dU = (gt.double()[:, None] * (2.0 * wt * proj)[None, :]).float()
+        res["backward_ms"], _ = timed(lambda: ctx.backward(dU))
+        ctx.close()
+        u0, u1 = U0.double().cpu().numpy(), U1.double().cpu().numpy()
+        res["sin_tape_vs_plain"] = sin_max(u0, u1)
+    del A
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args):
@@ -488,8 +596,10 @@ def run_ours(args):
     k = HEAD["k"]
     t = time_problem(torch, pod, A_np, HEAD, args.steps, args.warmup, dev, world, detail=True)
     hbm, bf16, bf16_sus, peak_kind = load_peaks()
-    roof = roofline_of(t, m, n, k, hbm, bf16)
+    roof = roofline_of(t, m, n, k, hbm, bf16, tc_proj=True)
     roof["peak_source"] = roof.get("peak_source", "%s: MEASURED_PEAKS.json hbm_gbs" % peak_kind)
+    roof["tensor_peak_source"] = ("%s: MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio (1.1 / 2.25)"
+                                  % peak_kind)
     core_phase = np.mean(np.array(t["core_cyc"], dtype=np.float64), axis=0).tolist()
     # the FP32 flow workload beside it
     F_np = make_flow()
@@ -498,6 +608,8 @@ def run_ours(args):
             "c": FLOW["c"], "rounds": tf["rounds"], "ms_per_step": tf["ms"], "e2e_ms": tf["ms_e2e"],
             "gpu_launches": int(tf["launches"])}
     del F_np
+    forms = precision_forms(torch, pod, A_np, HEAD, dev) if world == 1 else None
+    diff = differentiable_form(torch, pod, dev) if world == 1 else None
     cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, ref = oracle_full(A_np, HEAD)
@@ -506,6 +618,13 @@ def run_ours(args):
                          "on the host cores" % len(ref.trace)}
         acc = accuracy(t["U"], t["sigma"], ref, k)
         acc["rounds_equal"] = int(len(ref.trace) == t["rounds"])
+        if forms:
+            for name, f in forms.items():
+                f["accuracy_vs_oracle"] = accuracy(f.pop("U"), f.pop("sigma"), ref, k)
+    if forms:
+        for f in forms.values():
+            f.pop("U", None)
+            f.pop("sigma", None)
     if rank == 0:
         line = {"metric": METRIC, "value": t["ms"] / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t["ms"], "higher_is_better": False, "scaling": "weak",
@@ -526,6 +645,8 @@ def run_ours(args):
                                  core_phase)}},
                 "roofline": roof,
                 "flow_316": flow,
+                "precision_forms": forms,
+                "differentiable_form": diff,
                 "clocks": t["clocks"],
                 "cpu_baseline": cpu}
         print(json.dumps(line))

@@ -170,6 +170,34 @@ __device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) {
     return df_fast_two_sum(q1, q2);
 }
 
+// Accumulator of a sum of products (a dot product) over X.  X = double: FMA.
+// X = dfloat: the compensated dot product "Dot2" of Ogita, Rump and Oishi
+// (SIAM J. Sci. Comput. 26, 2005): the rounded sum s is carried with TwoSum,
+// the rounding errors of the sums and of the products (TwoProduct, plus the
+// low-part cross terms of the double-float operands) are collected in c; the
+// result s + c is as accurate as a sum taken in twice the working precision,
+// with a dependent chain of about eight FP32 operations per term instead of
+// the ~20 of a double-float add.  Two accumulators per loop (even and odd
+// terms) let the chains overlap.
+template <typename X> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<dfloat> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(dfloat a, dfloat b) {
+        const float p = a.hi * b.hi;
+        const float e = fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi);
+        const float t = s + p;
+        const float bb = t - s;
+        c += ((s - (t - bb)) + (p - bb)) + e;
+        s = t;
+    }
+    __device__ __forceinline__ dfloat get() const { return df_fast_two_sum(s, c); }
+};
+
 // Scalar traits: the small dense algebra is written once over X = double
 // (FP64 path) or X = dfloat (FP32 path).
 template <typename X> struct XOps;

@@ -359,25 +359,34 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
             const bool valid = active && q < ncol;
             float4 *bp = reinterpret_cast<float4 *>(B + (size_t)p * LD);
             float4 *bq = reinterpret_cast<float4 *>(B + (size_t)(valid ? q : p) * LD);
-            float4 x[KG], y[KG];
-#pragma unroll
-            for (int k = 0; k < KG; ++k) {
-                x[k] = bp[off[k]];
-                y[k] = bq[off[k]];
-            }
             const float a = alpha[p], b = alpha[valid ? q : p];
-            float g0 = 0.f, g1 = 0.f;
+            // a pair counted as converged (both rows trailing) loads nothing;
+            // its lanes still take part in the shuffles
+            const bool work = valid && (a >= thr || b >= thr);
+            // wide rows (KG > 4) are read again for the rotation instead of
+            // being held in registers across the reduction
+            constexpr int KH = KG > 4 ? 1 : KG;
+            float4 x[KH], y[KH];
+            float g = 0.f;
+            if (work) {
+                float g0 = 0.f, g1 = 0.f;
 #pragma unroll
-            for (int k = 0; k < KG; ++k) {
-                g0 = fmaf(x[k].x, y[k].x, g0);
-                g1 = fmaf(x[k].y, y[k].y, g1);
-                g0 = fmaf(x[k].z, y[k].z, g0);
-                g1 = fmaf(x[k].w, y[k].w, g1);
+                for (int k = 0; k < KG; ++k) {
+                    const float4 xv = bp[off[k]], yv = bq[off[k]];
+                    if constexpr (KH == KG) {
+                        x[k] = xv;
+                        y[k] = yv;
+                    }
+                    g0 = fmaf(xv.x, yv.x, g0);
+                    g1 = fmaf(xv.y, yv.y, g1);
+                    g0 = fmaf(xv.z, yv.z, g0);
+                    g1 = fmaf(xv.w, yv.w, g1);
+                }
+                g = g0 + g1;
             }
-            float g = g0 + g1;
             g += __shfl_xor_sync(0xffffffffu, g, 2, LP);
             g += __shfl_xor_sync(0xffffffffu, g, 1, LP);
-            if (valid && (a >= thr || b >= thr)) {
+            if (work) {
                 const float ab = a * b, g2 = g * g;
                 if (ab > 0.f && g2 > loose2 * ab && lp == 0) s_flag[1] = 1;
                 if (ab > 0.f && g2 > tol2 * ab) {
@@ -394,10 +403,18 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
                     const float t = sn * iy;
 #pragma unroll
                     for (int k = 0; k < KG; ++k) {
-                        bp[off[k]] = make_float4(fmaf(cs, x[k].x, -sn * y[k].x), fmaf(cs, x[k].y, -sn * y[k].y),
-                                                 fmaf(cs, x[k].z, -sn * y[k].z), fmaf(cs, x[k].w, -sn * y[k].w));
-                        bq[off[k]] = make_float4(fmaf(sn, x[k].x, cs * y[k].x), fmaf(sn, x[k].y, cs * y[k].y),
-                                                 fmaf(sn, x[k].z, cs * y[k].z), fmaf(sn, x[k].w, cs * y[k].w));
+                        float4 xk, yk;
+                        if constexpr (KH == KG) {
+                            xk = x[k];
+                            yk = y[k];
+                        } else {
+                            xk = bp[off[k]];
+                            yk = bq[off[k]];
+                        }
+                        bp[off[k]] = make_float4(fmaf(cs, xk.x, -sn * yk.x), fmaf(cs, xk.y, -sn * yk.y),
+                                                 fmaf(cs, xk.z, -sn * yk.z), fmaf(cs, xk.w, -sn * yk.w));
+                        bq[off[k]] = make_float4(fmaf(sn, xk.x, cs * yk.x), fmaf(sn, xk.y, cs * yk.y),
+                                                 fmaf(sn, xk.z, cs * yk.z), fmaf(sn, xk.w, cs * yk.w));
                     }
                     if (WITHV) {
                         float4 *vp = reinterpret_cast<float4 *>(V + (size_t)p * LD);
@@ -1350,19 +1367,30 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
             const J *bs = B + (size_t)order[s] * ldj;
-            X acc = XOps<X>::zero();
-            if (p < r) acc = Ex[p * nc + p] * XOps<X>::from_f((float)bs[p]);
-            for (int j = p < r ? r : p; j < nc; ++j) acc = acc + Ex[j * nc + p] * XOps<X>::from_f((float)bs[j]);
-            Vr[s * nc + p] = acc;
+            Acc<X> a0, a1;
+            if (p < r) a0.add(Ex[p * nc + p], XOps<X>::from_f((float)bs[p]));
+            int j = p < r ? r : p;
+            for (; j + 1 < nc; j += 2) {
+                a0.add(Ex[j * nc + p], XOps<X>::from_f((float)bs[j]));
+                a1.add(Ex[(j + 1) * nc + p], XOps<X>::from_f((float)bs[j + 1]));
+            }
+            if (j < nc) a0.add(Ex[j * nc + p], XOps<X>::from_f((float)bs[j]));
+            Vr[s * nc + p] = a0.get() + a1.get();
         }
         __syncthreads();
         const int rm = a.rmax;
         for (int e = tid; e < rsel * rsel; e += bd) {
             const int i = e / rsel, j = e % rsel;
-            X acc = XOps<X>::zero();
-            if (i <= j)
-                for (int p = 0; p < nc; ++p) acc = acc + Vr[i * nc + p] * Vr[j * nc + p];
-            Gb[i * rm + j] = acc;
+            Acc<X> a0, a1;
+            if (i <= j) {
+                int p = 0;
+                for (; p + 1 < nc; p += 2) {
+                    a0.add(Vr[i * nc + p], Vr[j * nc + p]);
+                    a1.add(Vr[i * nc + p + 1], Vr[j * nc + p + 1]);
+                }
+                if (p < nc) a0.add(Vr[i * nc + p], Vr[j * nc + p]);
+            }
+            Gb[i * rm + j] = a0.get() + a1.get();
         }
         __syncthreads();
         // CholeskyQR of Vr.  Its columns are nearly orthogonal (the rotated
@@ -1475,9 +1503,14 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         }
         for (int e = tid; e < nc * rsel; e += bd) {
             const int s = e / nc, p = e % nc;
-            X acc = XOps<X>::zero();
-            for (int l = 0; l <= s; ++l) acc = acc + Vr[l * nc + p] * Mb[l * a.rmax + s];
-            Q[s * nc + p] = acc;
+            Acc<X> a0, a1;
+            int l = 0;
+            for (; l + 1 <= s; l += 2) {
+                a0.add(Vr[l * nc + p], Mb[l * a.rmax + s]);
+                a1.add(Vr[(l + 1) * nc + p], Mb[(l + 1) * a.rmax + s]);
+            }
+            if (l <= s) a0.add(Vr[l * nc + p], Mb[l * a.rmax + s]);
+            Q[s * nc + p] = a0.get() + a1.get();
         }
         __syncthreads();
         for (int e = tid; e < nc * rsel; e += bd) {
@@ -1487,7 +1520,14 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
             if (j < r) {
                 acc = Ex[j * nc + j] * Q[s * nc + j];
             } else {
-                for (int p = 0; p <= j; ++p) acc = acc + Ex[j * nc + p] * Q[s * nc + p];
+                Acc<X> a0, a1;
+                int p = 0;
+                for (; p + 1 <= j; p += 2) {
+                    a0.add(Ex[j * nc + p], Q[s * nc + p]);
+                    a1.add(Ex[j * nc + p + 1], Q[s * nc + p + 1]);
+                }
+                if (p <= j) a0.add(Ex[j * nc + p], Q[s * nc + p]);
+                acc = a0.get() + a1.get();
             }
             Yt[s * nc + j] = acc;
         }

@@ -66,9 +66,22 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Copy rows [i0, i0 + bm) of `ncols` columns into dst (column-major, ld),
-// zero-filling rows at or beyond `mend`.  vec: 16-byte copies are legal.
-// `live(c)` false makes column c read as zeros (nothing is fetched).
+// Slab layout in shared memory: column-major with leading dimension ld = bm,
+// the 4-element row chunks of column c XOR-swizzled by (c / 4) mod 8 (masked
+// to the chunks a column has): chunk q of column c sits at chunk q ^ sw(c).
+// The 4 x 4 tiles give consecutive threads columns 4 apart, so without the
+// swizzle (or with the old 4-element pad) a warp's 16-byte loads fell on two
+// bank groups (16-way conflicts); with it they cover all eight.
+__host__ __device__ inline int sw_mask(int bm) { return (bm >> 2) - 1 < 7 ? (bm >> 2) - 1 : 7; }
+// position of row i (0 <= i < bm) of column c inside that column
+__device__ __forceinline__ int swz(int c, int i, int mask) {
+    return ((((i >> 2) ^ ((c >> 2) & mask)) << 2) | (i & 3));
+}
+
+// Copy rows [i0, i0 + bm) of `ncols` columns into dst (the swizzled slab
+// layout above, ld), zero-filling rows at or beyond `mend`.  vec: 16-byte
+// copies are legal.  `live(c)` false makes column c read as zeros (nothing
+// is fetched).
 template <typename T, typename ColFn, typename LiveFn>
 __device__ __forceinline__ void issue_slab(T *dst, int ld, int ncols, int bm, int64_t i0, int64_t mend,
                                            bool vec, ColFn col, LiveFn live) {
@@ -82,7 +95,7 @@ __device__ __forceinline__ void issue_slab(T *dst, int ld, int ncols, int bm, in
             int bytes = left >= V ? 16 : (left > 0 ? (int)left * (int)sizeof(T) : 0);
             if (!live(c)) bytes = 0;
             const T *src = col(c) + (bytes > 0 ? row : 0);
-            cp_async16(dst + (size_t)c * ld + q * V, src, bytes);
+            cp_async16(dst + (size_t)c * ld + swz(c, q * V, sw_mask(bm)), src, bytes);
         }
     } else {
         for (int e = threadIdx.x; e < ncols * bm; e += blockDim.x) {
@@ -90,7 +103,7 @@ __device__ __forceinline__ void issue_slab(T *dst, int ld, int ncols, int bm, in
             const int64_t row = i0 + q;
             const int bytes = (row < mend && live(c)) ? (int)sizeof(T) : 0;
             const T *src = col(c) + (bytes > 0 ? row : 0);
-            cp_async_small<sizeof(T)>(dst + (size_t)c * ld + q, src, bytes);
+            cp_async_small<sizeof(T)>(dst + (size_t)c * ld + swz(c, q, sw_mask(bm)), src, bytes);
         }
     }
 }
@@ -149,6 +162,7 @@ template <typename T>
 __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm, bool sym, double *acc,
                          int ldacc, T *red) {
     const int tid = threadIdx.x, bd = blockDim.x;
+    const int msk = sw_mask(bm);
     const int ta = (na + 3) >> 2, tb = (nb + 3) >> 2;
     // only the tiles that are computed (the upper triangle when sym) share out the threads
     const int nT = sym ? tb * (tb + 1) / 2 : ta * tb;
@@ -164,9 +178,9 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
             for (int rc = 0; rc < chunks; ++rc) {
                 T x[4][4], y[4][4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + ((rc ^ (ti & msk)) << 2), x[u]);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) lds4(Y + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
+                for (int v = 0; v < 4; ++v) lds4(Y + (size_t)(4 * tj + v) * ld + ((rc ^ (tj & msk)) << 2), y[v]);
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -193,9 +207,9 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
         for (int rc = grp; rc < chunks; rc += RG) {
             T x[4][4], y[4][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+            for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + ((rc ^ (ti & msk)) << 2), x[u]);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) lds4(Y + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
+            for (int v = 0; v < 4; ++v) lds4(Y + (size_t)(4 * tj + v) * ld + ((rc ^ (tj & msk)) << 2), y[v]);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -226,6 +240,7 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 template <typename T>
 __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, int ldacc) {
     const int ta = (na + 3) >> 2, nT = ta * ta, chunks = bm >> 2;
+    const int msk = sw_mask(bm);
     for (int tile = threadIdx.x; tile < nT; tile += blockDim.x) {
         const int ti = tile / ta, tj = tile - ti * ta;
         if (ti > tj) continue;
@@ -236,9 +251,9 @@ __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, i
             for (int rc = 0; rc < chunks; ++rc) {
                 float x[4][4], y[4][4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + ((rc ^ (ti & msk)) << 2), x[u]);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) lds4(X + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
+                for (int v = 0; v < 4; ++v) lds4(X + (size_t)(4 * tj + v) * ld + ((rc ^ (tj & msk)) << 2), y[v]);
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -264,9 +279,9 @@ __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, i
             for (int rc = 0; rc < chunks; ++rc) {
                 double x[4][4], y[4][4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + 4 * rc, x[u]);
+                for (int u = 0; u < 4; ++u) lds4(X + (size_t)(4 * ti + u) * ld + ((rc ^ (ti & msk)) << 2), x[u]);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) lds4(X + (size_t)(4 * tj + v) * ld + 4 * rc, y[v]);
+                for (int v = 0; v < 4; ++v) lds4(X + (size_t)(4 * tj + v) * ld + ((rc ^ (tj & msk)) << 2), y[v]);
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -292,7 +307,7 @@ template <typename T, typename Store>
 __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K1, const T *S1, int ls1,
                                                const T *A2, int K2, const T *S2, int ls2, int ld, bool tri,
                                                Store store) {
-    const int chunks = bm >> 2, tn = (N + 3) >> 2;
+    const int chunks = bm >> 2, tn = (N + 3) >> 2, msk = sw_mask(bm);
     for (int tile = threadIdx.x; tile < chunks * tn; tile += blockDim.x) {
         const int rc = tile % chunks, cj = tile / chunks;
         T a1[4][4], a2[4][4];
@@ -303,7 +318,7 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
         const int k1end = tri ? min(K1, 4 * cj + 4) : K1;
         for (int k = 0; k < k1end; ++k) {
             T x[4], s[4];
-            lds4(A1 + (size_t)k * ld + 4 * rc, x);
+            lds4(A1 + (size_t)k * ld + ((rc ^ ((k >> 2) & msk)) << 2), x);
             lds4(S1 + (size_t)k * ls1 + 4 * cj, s);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -312,7 +327,7 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
         }
         for (int k = 0; k < K2; ++k) {
             T x[4], s[4];
-            lds4(A2 + (size_t)k * ld + 4 * rc, x);
+            lds4(A2 + (size_t)k * ld + ((rc ^ ((k >> 2) & msk)) << 2), x);
             lds4(S2 + (size_t)k * ls2 + 4 * cj, s);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -334,7 +349,7 @@ struct SmemPlan {
 
 __host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm) {
     SmemPlan p;
-    p.ld = bm + 4;
+    p.ld = bm;
     p.r4 = round4(rmax);
     p.c4 = round4(cmax);
     p.buf = (size_t)(p.r4 + p.c4) * p.ld;
@@ -486,7 +501,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     const int r = st->r_cur, g = st->g, rn = st->r_new;
     const int bm = a.bm;
     const SmemPlan L = smem_plan(a.rmax, a.cmax, bm);
-    const int ld = L.ld;
+    const int ld = L.ld, msk = sw_mask(bm);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf0 = reinterpret_cast<T *>(smem_raw);
     T *buf1 = buf0 + L.buf;
@@ -581,7 +596,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                                   [&](int rc, int cj, T (&a1)[4][4], T (&)[4][4]) {
 #pragma unroll
                                       for (int v = 0; v < 4; ++v) {
-                                          T *p = Cs + (size_t)(4 * cj + v) * ld + 4 * rc;
+                                          T *p = Cs + (size_t)(4 * cj + v) * ld + ((rc ^ (cj & msk)) << 2);
                                           T z[4];
                                           lds4(p, z);
 #pragma unroll
@@ -600,7 +615,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                                   [&](int rc, int cj, T (&a1)[4][4], T (&a2)[4][4]) {
 #pragma unroll
                                       for (int v = 0; v < 4; ++v) {
-                                          T *p = Cs + (size_t)(4 * cj + v) * ld + 4 * rc;
+                                          T *p = Cs + (size_t)(4 * cj + v) * ld + ((rc ^ (cj & msk)) << 2);
                                           T z[4];
                                           lds4(p, z);
 #pragma unroll
@@ -617,7 +632,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                                       T w[4];
 #pragma unroll
                                       for (int u = 0; u < 4; ++u) w[u] = a1[u][v];
-                                      sts4(Ws + (size_t)(4 * cj + v) * ld + 4 * rc, w);
+                                      sts4(Ws + (size_t)(4 * cj + v) * ld + ((rc ^ (cj & msk)) << 2), w);
                                   }
                               });
             __syncthreads();
@@ -628,7 +643,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                 const int nrow = left < bm ? (int)left : bm;
                 for (int e = tid; e < g * bm; e += bd) {
                     const int j = e / bm, i = e - j * bm;
-                    if (i < nrow) a.Wout[(int64_t)j * a.ldw + i0 + i] = Ws[(size_t)j * ld + i];
+                    if (i < nrow) a.Wout[(int64_t)j * a.ldw + i0 + i] = Ws[(size_t)j * ld + swz(j, i, msk)];
                 }
             }
             gram_acc<T>(Ws, g, Ws, g, ld, bm, true, acc2, L.c4, red);
@@ -723,7 +738,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_atu(AtuArgs<T> a, int nb, int 
     const int64_t ib = (int64_t)blockIdx.y * rows_per;
     const int64_t ie = (ib + rows_per) < a.m ? (ib + rows_per) : a.m;
     const int nb4 = round4(nb), r4 = round4(a.rmax);
-    const int ld = bm + 4;
+    const int ld = bm;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf0 = reinterpret_cast<T *>(smem_raw);
     const size_t bsz = (size_t)(nb4 + r4) * ld;
@@ -895,7 +910,7 @@ AtuPlan atu_plan(int dtype, int64_t m, int64_t n, int rmax, int num_sms) {
     p.bm = 128;
     const int nb4 = round4(p.nb), r4 = round4(rmax);
     for (;;) {
-        p.smem = 2 * (size_t)(nb4 + r4) * (p.bm + 4) * es + (size_t)nb4 * r4 * 8 + TALL_THREADS * 16 * es + 64;
+        p.smem = 2 * (size_t)(nb4 + r4) * p.bm * es + (size_t)nb4 * r4 * 8 + TALL_THREADS * 16 * es + 64;
         if (p.smem <= 110 * 1024 || p.bm <= 16) break;
         p.bm >>= 1;
     }
