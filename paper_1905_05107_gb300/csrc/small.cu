@@ -359,34 +359,25 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
             const bool valid = active && q < ncol;
             float4 *bp = reinterpret_cast<float4 *>(B + (size_t)p * LD);
             float4 *bq = reinterpret_cast<float4 *>(B + (size_t)(valid ? q : p) * LD);
-            const float a = alpha[p], b = alpha[valid ? q : p];
-            // a pair counted as converged (both rows trailing) loads nothing;
-            // its lanes still take part in the shuffles
-            const bool work = valid && (a >= thr || b >= thr);
-            // wide rows (KG > 4) are read again for the rotation instead of
-            // being held in registers across the reduction
-            constexpr int KH = KG > 4 ? 1 : KG;
-            float4 x[KH], y[KH];
-            float g = 0.f;
-            if (work) {
-                float g0 = 0.f, g1 = 0.f;
+            float4 x[KG], y[KG];
 #pragma unroll
-                for (int k = 0; k < KG; ++k) {
-                    const float4 xv = bp[off[k]], yv = bq[off[k]];
-                    if constexpr (KH == KG) {
-                        x[k] = xv;
-                        y[k] = yv;
-                    }
-                    g0 = fmaf(xv.x, yv.x, g0);
-                    g1 = fmaf(xv.y, yv.y, g1);
-                    g0 = fmaf(xv.z, yv.z, g0);
-                    g1 = fmaf(xv.w, yv.w, g1);
-                }
-                g = g0 + g1;
+            for (int k = 0; k < KG; ++k) {
+                x[k] = bp[off[k]];
+                y[k] = bq[off[k]];
             }
+            const float a = alpha[p], b = alpha[valid ? q : p];
+            float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < KG; ++k) {
+                g0 = fmaf(x[k].x, y[k].x, g0);
+                g1 = fmaf(x[k].y, y[k].y, g1);
+                g0 = fmaf(x[k].z, y[k].z, g0);
+                g1 = fmaf(x[k].w, y[k].w, g1);
+            }
+            float g = g0 + g1;
             g += __shfl_xor_sync(0xffffffffu, g, 2, LP);
             g += __shfl_xor_sync(0xffffffffu, g, 1, LP);
-            if (work) {
+            if (valid && (a >= thr || b >= thr)) {
                 const float ab = a * b, g2 = g * g;
                 if (ab > 0.f && g2 > loose2 * ab && lp == 0) s_flag[1] = 1;
                 if (ab > 0.f && g2 > tol2 * ab) {
@@ -403,18 +394,10 @@ __device__ int jacobi_lean(float *B, int ncol, float *V, float *alpha, float tol
                     const float t = sn * iy;
 #pragma unroll
                     for (int k = 0; k < KG; ++k) {
-                        float4 xk, yk;
-                        if constexpr (KH == KG) {
-                            xk = x[k];
-                            yk = y[k];
-                        } else {
-                            xk = bp[off[k]];
-                            yk = bq[off[k]];
-                        }
-                        bp[off[k]] = make_float4(fmaf(cs, xk.x, -sn * yk.x), fmaf(cs, xk.y, -sn * yk.y),
-                                                 fmaf(cs, xk.z, -sn * yk.z), fmaf(cs, xk.w, -sn * yk.w));
-                        bq[off[k]] = make_float4(fmaf(sn, xk.x, cs * yk.x), fmaf(sn, xk.y, cs * yk.y),
-                                                 fmaf(sn, xk.z, cs * yk.z), fmaf(sn, xk.w, cs * yk.w));
+                        bp[off[k]] = make_float4(fmaf(cs, x[k].x, -sn * y[k].x), fmaf(cs, x[k].y, -sn * y[k].y),
+                                                 fmaf(cs, x[k].z, -sn * y[k].z), fmaf(cs, x[k].w, -sn * y[k].w));
+                        bq[off[k]] = make_float4(fmaf(sn, x[k].x, cs * y[k].x), fmaf(sn, x[k].y, cs * y[k].y),
+                                                 fmaf(sn, x[k].z, cs * y[k].z), fmaf(sn, x[k].w, cs * y[k].w));
                     }
                     if (WITHV) {
                         float4 *vp = reinterpret_cast<float4 *>(V + (size_t)p * LD);
