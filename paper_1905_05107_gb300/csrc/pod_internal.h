@@ -100,11 +100,14 @@ enum TallKind { TALL_PROJ = 0, TALL_CGS = 1, TALL_QR2 = 2, TALL_UPDATE = 3 };
 
 struct TallPlan {
     int grid;
-    int bm;
+    int bm;                 // slab rows of the PROJ pass (see bm_k)
     int groups;
-    size_t smem;
-    int wide;               // coefficient tiles and FP64 accumulators in global scratch
-    int64_t gstride;        // bytes of scratch per CTA (wide plans)
+    size_t smem;            // the largest of smem_k
+    int wide;               // some kind keeps coefficient tiles and FP64 accumulators in global scratch
+    int64_t gstride;        // bytes of scratch per CTA (wide kinds)
+    int bm_k[4];            // per TallKind: slab rows,
+    size_t smem_k[4];       //   dynamic shared memory,
+    int wide_k[4];          //   whether it uses the global scratch
 };
 
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms);

@@ -520,256 +520,127 @@ __device__ void sort_desc(const K *key, int n, int *order) {
     __syncthreads();
 }
 
-// Largest singular value of B (nrow x k, column-major, ld), i.e. the square
-// root of the largest eigenvalue of M = B^T B (k x k):
-//  * M is formed and scaled by a power of two to max_i M_ii in [1/2, 1);
-//  * Lanczos with full reorthogonalisation (two classical Gram-Schmidt passes
-//    against every earlier vector per step), started from q_i ~ sqrt(M_ii),
-//    for min(k, LZ_STEPS) steps or until the Krylov space closes; the
-//    reorthogonalised coefficients give the tridiagonal T (alpha, beta);
-//  * the largest eigenvalue of T by multisection with Sturm sign counts
-//    (one warp, 32 points per pass, division-free recurrence with power-of-
-//    two rescaling), clamped to [trace(M) / k, trace(M)], the bounds any
-//    largest eigenvalue of M obeys.
-// Every inner product of a step is split over groups of 8 threads.  B's
-// storage is reused for the Lanczos vectors (B is not needed after M).
-// Work arrays: M k^2, alpha and beta LZ_STEPS + 1 each, wv k, cv 2 (LZ_STEPS
-// + 1).  Called by the whole CTA; the result is valid in threads 0..31.
-constexpr int LZ_STEPS = 64;
-constexpr int LZ_WARP_K = 64;   // k up to this: the one-warp Lanczos
-constexpr int LZ_LDQ = 65;      // its leading dimension (odd: bank-disjoint)
-__host__ __device__ inline size_t lz_warp_words(int rmax) {
-    return rmax <= LZ_WARP_K ? (size_t)rmax * LZ_LDQ + LZ_WARP_K + 2 * LZ_LDQ : 0;
-}
+// Largest singular value of B (nrow x k), the square root of the largest
+// eigenvalue lambda_1 of the k x k matrix M = B^T B:
+//  * M from B stored row by row (Bt[p k + i] = B[p][i]: consecutive threads
+//    read consecutive entries);
+//  * P = M / trace(M), then repeated squaring P <- P^2 / trace(P^2): after s
+//    squarings P is M^(2^s) normalised, whose eigenvalues are
+//    (lambda_i / lambda_1)^(2^s) relative to the top one, so P approaches the
+//    projector on the top eigenvector; it stops when trace(P^2) > 1 - eps
+//    (one eigenvalue left) or after SQ_MAX squarings (M^16384);
+//  * x = the column of P with the largest diagonal, refined by SQ_APPLY
+//    products with P (each worth 2^s power steps), then the Rayleigh quotient
+//    x^T M x / x^T x with the original M: a lower bound of lambda_1 whose
+//    error is (lambda_1 - lambda_j) times the square of x's residual
+//    components, clamped to [trace(M) / k, trace(M)], bounds any lambda_1 of
+//    M obeys.  A degenerate top eigenvalue needs no separation: any vector of
+//    its eigenspace gives it exactly.
+// The power iteration this replaces (16 plain steps) under-read sin(theta)
+// by up to 1.4e-3 when the top two singular values of B were close; a
+// Lanczos version with full reorthogonalisation was exact but cost ~4 k
+// thousand cycles per core.
+// Work arrays: M, P, P2 k^2 each, x and y k each.  Called by the whole CTA;
+// the result is valid in every thread.
+constexpr int SQ_MAX = 14;
+constexpr int SQ_APPLY = 4;
 
 template <typename J>
-__device__ int sturm_below(const J *al, const J *be, int s, J x) {
-    // number of eigenvalues of T below x: sign changes of the leading minors
-    // P_0 = 1, P_1 = al_0 - x, P_{i+1} = (al_i - x) P_i - be_{i-1}^2 P_{i-1};
-    // a zero minor takes the sign opposite to the one before it
-    const J big = sizeof(J) == 4 ? (J)1e30 : (J)1e250, small_ = sizeof(J) == 4 ? (J)1e-30 : (J)1e-250;
-    const J resc = sizeof(J) == 4 ? (J)1e-30 : (J)1e-250, grow = sizeof(J) == 4 ? (J)1e30 : (J)1e250;
-    J p0 = 1, p1 = al[0] - x;
-    int cnt = 0;
-    bool s0 = true;                       // sign of p0 (true = positive)
-    bool s1 = p1 > (J)0 || (p1 == (J)0 && !s0);
-    cnt += (s1 != s0);
-    for (int i = 1; i < s; ++i) {
-        J p2 = (al[i] - x) * p1 - be[i - 1] * be[i - 1] * p0;
-        const bool s2 = p2 > (J)0 || (p2 == (J)0 && !s1);
-        cnt += (s2 != s1);
-        p0 = p1;
-        p1 = p2;
-        s1 = s2;
-        const J ap = fabs(p1) > fabs(p0) ? fabs(p1) : fabs(p0);
-        if (ap > big) {
-            p0 *= resc;
-            p1 *= resc;
-        } else if (ap < small_ && ap > (J)0) {
-            p0 *= grow;
-            p1 *= grow;
-        }
-    }
-    return cnt;
-}
-
-template <typename J>
-__device__ double top_singular_value(J *B, int ld, int nrow, int k, J *M, J *alpha, J *beta, J *wv, J *cv,
-                                     J *lzq, double *red_d) {
+__device__ void sq_matmul(const J *A, J *C, int k) {
+    // C = A A for symmetric A (k x k, row-major); four partial sums per entry
     const int tid = threadIdx.x, bd = blockDim.x;
-    const int lane8 = tid & 7, grp = tid >> 3, ngrp = bd >> 3;
+    for (int e = tid; e < k * k; e += bd) {
+        const int i = e / k, j = e - i * k;
+        J v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+        int t = 0;
+        for (; t + 4 <= k; t += 4) {
+            v0 = fma(A[i * k + t], A[t * k + j], v0);
+            v1 = fma(A[i * k + t + 1], A[(t + 1) * k + j], v1);
+            v2 = fma(A[i * k + t + 2], A[(t + 2) * k + j], v2);
+            v3 = fma(A[i * k + t + 3], A[(t + 3) * k + j], v3);
+        }
+        for (; t < k; ++t) v0 = fma(A[i * k + t], A[t * k + j], v0);
+        C[e] = (v0 + v1) + (v2 + v3);
+    }
+}
+
+template <typename J>
+__device__ double top_singular_value(const J *Bt, int nrow, int k, J *M, J *P, J *P2, J *x, J *y, double *red_d) {
+    const int tid = threadIdx.x, bd = blockDim.x;
     J *red = reinterpret_cast<J *>(red_d);
     for (int e = tid; e < k * k; e += bd) {
-        const int i = e / k, j = e % k;
-        J s = 0;
-        for (int p = 0; p < nrow; ++p) s = fma(B[(size_t)i * ld + p], B[(size_t)j * ld + p], s);
-        M[i * k + j] = s;
-    }
-    __syncthreads();
-    J dmax = 0, tr = 0;
-    for (int i = 0; i < k; ++i) {
-        dmax = M[i * k + i] > dmax ? M[i * k + i] : dmax;
-        tr += M[i * k + i];
-    }
-    if (!(dmax > (J)0)) return 0.0;   // B = 0 (or not finite)
-    int ex;
-    frexp((double)dmax, &ex);
-    const J sc = (J)ldexp(1.0, -ex);    // M * sc has max diagonal in [1/2, 1)
-    tr *= sc;
-    __syncthreads();
-    for (int e = tid; e < k * k; e += bd) M[e] *= sc;
-    const int smax = k < LZ_STEPS ? k : LZ_STEPS;
-    const J eps = sizeof(J) == 4 ? (J)1.2e-7 : (J)2.3e-16;
-    int s = 0;
-    __syncthreads();
-    if (k <= LZ_WARP_K) {
-        // one warp, no CTA barriers: lane i holds rows i and i + 32 of each
-        // product; Lanczos vector l is column l of QT (k x LZ_LDQ, the odd
-        // leading dimension keeps a warp's accesses to distinct banks)
-        if (tid < 32) {
-            const int lane = tid;
-            J *QT = lzq, *w = lzq + (size_t)k * LZ_LDQ, *c0 = w + LZ_WARP_K;
-            J nrm0 = 0;
-            for (int i = 0; i < k; ++i) nrm0 += M[i * k + i];
-            const J inv0 = (J)1 / sqrt(nrm0);
-            for (int i = lane; i < k; i += 32) QT[i * LZ_LDQ] = sqrt(M[i * k + i]) * inv0;
-            __syncwarp();
-            for (int j = 0; j < smax; ++j) {
-                // four partial sums per product: the chains of dependent
-                // FMAs (and their shared-memory loads) overlap four ways
-                for (int i = lane; i < k; i += 32) {      // w = M q_j (M symmetric: read M[t][i])
-                    J v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-                    int t = 0;
-                    for (; t + 4 <= k; t += 4) {
-                        v0 = fma(M[t * k + i], QT[t * LZ_LDQ + j], v0);
-                        v1 = fma(M[(t + 1) * k + i], QT[(t + 1) * LZ_LDQ + j], v1);
-                        v2 = fma(M[(t + 2) * k + i], QT[(t + 2) * LZ_LDQ + j], v2);
-                        v3 = fma(M[(t + 3) * k + i], QT[(t + 3) * LZ_LDQ + j], v3);
-                    }
-                    for (; t < k; ++t) v0 = fma(M[t * k + i], QT[t * LZ_LDQ + j], v0);
-                    w[i] = (v0 + v1) + (v2 + v3);
-                }
-                __syncwarp();
-                for (int pass = 0; pass < 2; ++pass) {
-                    J *c = c0 + pass * LZ_LDQ;
-                    for (int l = lane; l <= j; l += 32) {   // c_l = q_l^T w
-                        J v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-                        int i = 0;
-                        for (; i + 4 <= k; i += 4) {
-                            v0 = fma(QT[i * LZ_LDQ + l], w[i], v0);
-                            v1 = fma(QT[(i + 1) * LZ_LDQ + l], w[i + 1], v1);
-                            v2 = fma(QT[(i + 2) * LZ_LDQ + l], w[i + 2], v2);
-                            v3 = fma(QT[(i + 3) * LZ_LDQ + l], w[i + 3], v3);
-                        }
-                        for (; i < k; ++i) v0 = fma(QT[i * LZ_LDQ + l], w[i], v0);
-                        c[l] = (v0 + v1) + (v2 + v3);
-                    }
-                    __syncwarp();
-                    for (int i = lane; i < k; i += 32) {    // w -= sum_l c_l q_l
-                        J v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-                        int l = 0;
-                        for (; l + 4 <= j + 1; l += 4) {
-                            v0 = fma(c[l], QT[i * LZ_LDQ + l], v0);
-                            v1 = fma(c[l + 1], QT[i * LZ_LDQ + l + 1], v1);
-                            v2 = fma(c[l + 2], QT[i * LZ_LDQ + l + 2], v2);
-                            v3 = fma(c[l + 3], QT[i * LZ_LDQ + l + 3], v3);
-                        }
-                        for (; l <= j; ++l) v0 = fma(c[l], QT[i * LZ_LDQ + l], v0);
-                        w[i] -= (v0 + v1) + (v2 + v3);
-                    }
-                    __syncwarp();
-                }
-                J w2 = 0;
-                for (int i = lane; i < k; i += 32) w2 = fma(w[i], w[i], w2);
-                const J bnorm = sqrt(warp_sum(w2));
-                if (lane == 0) {
-                    alpha[j] = c0[j] + c0[LZ_LDQ + j];
-                    beta[j] = bnorm;
-                }
-                s = j + 1;
-                if (!(bnorm > (J)8 * eps * (J)k) || j + 1 == smax) break;
-                const J inv = (J)1 / bnorm;
-                for (int i = lane; i < k; i += 32) QT[i * LZ_LDQ + j + 1] = w[i] * inv;
-                __syncwarp();
-            }
-            __syncwarp();
+        const int i = e / k, j = e - i * k;
+        J v0 = 0, v1 = 0;
+        int p = 0;
+        for (; p + 2 <= nrow; p += 2) {
+            v0 = fma(Bt[p * k + i], Bt[p * k + j], v0);
+            v1 = fma(Bt[(p + 1) * k + i], Bt[(p + 1) * k + j], v1);
         }
-    } else {
-    J *Q = B;                           // Lanczos vectors, k apart
-    // q_0 ~ sqrt(M_ii)
-    J nrm0 = 0;
-    for (int i = 0; i < k; ++i) nrm0 += M[i * k + i];   // sum of squares of sqrt(M_ii)
-    const J inv0 = (J)1 / sqrt(nrm0);
-    for (int i = tid; i < k; i += bd) Q[i] = sqrt(M[i * k + i]) * inv0;
+        if (p < nrow) v0 = fma(Bt[p * k + i], Bt[p * k + j], v0);
+        M[e] = v0 + v1;
+    }
     __syncthreads();
-    for (int j = 0; j < smax; ++j) {
-        const J *qj = Q + (size_t)j * k;
-        // w = M q_j (the loops step by the CTA's group count from 0, so
-        // every lane of a warp runs the same iterations and takes part in
-        // every shuffle; groups past the end contribute zeros)
-        for (int i0 = 0; i0 < k; i0 += ngrp) {
-            const int i = i0 + grp;
+    J tr = 0;
+    for (int i = 0; i < k; ++i) tr += M[i * k + i];
+    if (!(tr > (J)0)) return 0.0;   // B = 0 (or not finite); every thread the same
+    const J eps = sizeof(J) == 4 ? (J)1e-6 : (J)1e-13;
+    const J itr = (J)1 / tr;
+    for (int e = tid; e < k * k; e += bd) P[e] = M[e] * itr;
+    __syncthreads();
+    J *cur = P, *nxt = P2;
+    for (int sq = 0; sq < SQ_MAX; ++sq) {
+        sq_matmul<J>(cur, nxt, k);
+        __syncthreads();
+        J t2 = 0;
+        for (int i = 0; i < k; ++i) t2 += nxt[i * k + i];   // trace(cur^2) = sum of squared eigenvalues
+        if (!(t2 > (J)0)) break;                              // (every thread the same)
+        __syncthreads();
+        const J it2 = (J)1 / t2;
+        for (int e = tid; e < k * k; e += bd) nxt[e] *= it2;
+        __syncthreads();
+        J *sw = cur;
+        cur = nxt;
+        nxt = sw;
+        if (t2 > (J)1 - eps) break;                           // one eigenvalue left
+    }
+    // x = the column of cur with the largest diagonal
+    int imax = 0;
+    J dmax = -1;
+    for (int i = 0; i < k; ++i)
+        if (cur[i * k + i] > dmax) {
+            dmax = cur[i * k + i];
+            imax = i;
+        }
+    for (int i = tid; i < k; i += bd) x[i] = cur[i * k + imax];
+    __syncthreads();
+    for (int it = 0; it < SQ_APPLY; ++it) {
+        for (int i = tid; i < k; i += bd) {
             J v = 0;
-            if (i < k)
-                for (int l = lane8; l < k; l += 8) v = fma(M[i * k + l], qj[l], v);
-            v += __shfl_xor_sync(0xffffffffu, v, 4);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            if (i < k && lane8 == 0) wv[i] = v;
+            for (int t = 0; t < k; ++t) v = fma(cur[i * k + t], x[t], v);
+            y[i] = v;
         }
         __syncthreads();
-        for (int pass = 0; pass < 2; ++pass) {
-            J *c = cv + pass * (LZ_STEPS + 1);
-            // c_l = q_l^T w, l <= j
-            for (int l0 = 0; l0 <= j; l0 += ngrp) {
-                const int l = l0 + grp;
-                J v = 0;
-                if (l <= j)
-                    for (int i = lane8; i < k; i += 8) v = fma(Q[(size_t)l * k + i], wv[i], v);
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                if (l <= j && lane8 == 0) c[l] = v;
-            }
-            __syncthreads();
-            // w -= sum_l c_l q_l
-            for (int i0 = 0; i0 < k; i0 += ngrp) {
-                const int i = i0 + grp;
-                J v = 0;
-                if (i < k)
-                    for (int l = lane8; l <= j; l += 8) v = fma(c[l], Q[(size_t)l * k + i], v);
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                if (i < k && lane8 == 0) wv[i] -= v;
-            }
-            __syncthreads();
-        }
-        J w2 = 0;
-        for (int i = tid; i < k; i += bd) w2 = fma(wv[i], wv[i], w2);
-        const J bnorm = sqrt(block_sum<J>(w2, red));
-        if (tid == 0) {
-            alpha[j] = cv[j] + cv[LZ_STEPS + 1 + j];
-            beta[j] = bnorm;
-        }
-        s = j + 1;
-        // the Krylov space closed (T's eigenvalues are M's within it)
-        if (!(bnorm > (J)8 * eps * (J)k) || j + 1 == smax) break;
-        const J inv = (J)1 / bnorm;
-        for (int i = tid; i < k; i += bd) Q[(size_t)(j + 1) * k + i] = wv[i] * inv;
+        J n2 = 0;
+        for (int t = 0; t < k; ++t) n2 = fma(y[t], y[t], n2);
+        const J in = n2 > (J)0 ? (J)1 / sqrt(n2) : (J)0;
+        __syncthreads();
+        for (int i = tid; i < k; i += bd) x[i] = y[i] * in;
         __syncthreads();
     }
+    // Rayleigh quotient with the original M
+    J num = 0;
+    for (int i = tid; i < k; i += bd) {
+        J v = 0;
+        for (int t = 0; t < k; ++t) v = fma(M[i * k + t], x[t], v);
+        num = fma(x[i], v, num);
     }
-    __syncthreads();
-    double result = 0.0;
-    if (tid < 32) {
-        // Gershgorin bounds of T (beta_0 .. beta_{s-2} couple its rows)
-        J lo = alpha[0], hi = alpha[0];
-        for (int i = 0; i < s; ++i) {
-            const J off = (i > 0 ? fabs(beta[i - 1]) : (J)0) + (i + 1 < s ? fabs(beta[i]) : (J)0);
-            lo = alpha[i] - off < lo ? alpha[i] - off : lo;
-            hi = alpha[i] + off > hi ? alpha[i] + off : hi;
-        }
-        const int passes = sizeof(J) == 4 ? 6 : 12;
-        for (int ps = 0; ps < passes; ++ps) {
-            const J x = lo + (hi - lo) * (J)(tid + 1) / (J)33;
-            const int cnt = sturm_below<J>(alpha, beta, s, x);
-            const unsigned above = __ballot_sync(0xffffffffu, cnt == s);   // x beyond the top eigenvalue
-            const int l0 = above ? __ffs(above) - 1 : 32;
-            const J xl = __shfl_sync(0xffffffffu, x, l0 > 0 ? l0 - 1 : 0);
-            const J xh = __shfl_sync(0xffffffffu, x, l0 < 32 ? l0 : 31);
-            const J nlo = l0 == 0 ? lo : xl;
-            const J nhi = l0 == 32 ? hi : xh;
-            lo = nlo;
-            hi = nhi;
-            if (hi - lo <= eps * (fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi))) break;
-        }
-        J lam = (J)0.5 * (lo + hi);
-        const J lower = tr / (J)k;
-        lam = lam < lower ? lower : (lam > tr ? tr : lam);
-        result = sqrt((double)lam / (double)sc);
-    }
-    return result;   // valid in threads 0..31
+    num = block_sum<J>(num, red);
+    J xx = 0;
+    for (int t = 0; t < k; ++t) xx = fma(x[t], x[t], xx);
+    J lam = xx > (J)0 ? num / xx : (J)0;
+    const J lower = tr / (J)k;
+    lam = lam < lower ? lower : (lam > tr ? tr : lam);
+    return sqrt((double)lam);
 }
 
 __host__ __device__ inline size_t al16x(size_t b) { return (b + 15) / 16 * 16; }
@@ -979,13 +850,10 @@ __host__ __device__ inline CoreLayout core_layout(int rmax, int cmax, int jsize)
     const size_t jb = (jsize == 4 && nmax <= LEAN_MAX) ? (size_t)lean_ld(nmax) * nmax : (size_t)nmax * nmax;
     L.phaseB = 2 * al16x(jb * jsize) + al16x((size_t)nmax * jsize) + al16x((size_t)nmax * 4);
     // Vr, Q, Yt: nmax x rmax X; Gb, Rb, Mw, Mb: rmax x rmax X; Bs: nmax x rmax J;
-    // BtB: rmax^2 J; xv, yv: max(rmax, LZ_STEPS + 1) J; Lanczos work: rmax +
-    // 2 (LZ_STEPS + 1) J; sig: rmax X; ord2: rmax int
-    const size_t lzv = (size_t)(rmax > LZ_STEPS + 1 ? rmax : LZ_STEPS + 1);
+    // BtB, Psq: rmax^2 J each; xv, yv: rmax J; sig: rmax X; ord2: rmax int
     L.phaseC = 3 * al16x((size_t)nmax * rmax * 8) + 4 * al16x((size_t)rmax * rmax * 8) +
-               al16x((size_t)nmax * rmax * jsize) + al16x((size_t)rmax * rmax * jsize) + 2 * al16x(lzv * jsize) +
-               al16x(((size_t)rmax + 2 * (LZ_STEPS + 1) + lz_warp_words(rmax)) * jsize) + al16x((size_t)rmax * 8) +
-               al16x((size_t)rmax * 4);
+               al16x((size_t)nmax * rmax * jsize) + 2 * al16x((size_t)rmax * rmax * jsize) + 2 * al16x((size_t)rmax * jsize) +
+               al16x((size_t)rmax * 8) + al16x((size_t)rmax * 4);
     const size_t bc = L.phaseB + L.phaseC;
     L.total = L.keep + (L.phaseA > bc ? L.phaseA : bc) + 64;
     return L;
@@ -1266,9 +1134,9 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     X *Mb = cv.take<X>((size_t)a.rmax * a.rmax);
     J *Bs = cv.take<J>((size_t)nmax * a.rmax);
     J *BtB = cv.take<J>((size_t)a.rmax * a.rmax);
-    J *xv = cv.take<J>(a.rmax > LZ_STEPS + 1 ? a.rmax : LZ_STEPS + 1);
-    J *yv = cv.take<J>(a.rmax > LZ_STEPS + 1 ? a.rmax : LZ_STEPS + 1);
-    J *lzw = cv.take<J>((size_t)a.rmax + 2 * (LZ_STEPS + 1) + lz_warp_words(a.rmax));
+    J *Psq = cv.take<J>((size_t)a.rmax * a.rmax);
+    J *xv = cv.take<J>(a.rmax);
+    J *yv = cv.take<J>(a.rmax);
     X *sig = cv.take<X>(a.rmax);
     int *ord2 = cv.take<int>(a.rmax);
     const bool f32 = sizeof(J) == 4;
@@ -1564,11 +1432,11 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
         if (a.criterion == POD_SUBSPACE) {
             for (int e = tid; e < nr * k; e += bd) {
                 const int cidx = e / nr, p = e % nr;
-                Bs[cidx * nr + p] = (J)XOps<X>::to(Q[cidx * nc + k + p]);
+                Bs[p * k + cidx] = (J)XOps<X>::to(Q[cidx * nc + k + p]);   // B row by row
             }
             __syncthreads();
-            const double smax =
-                top_singular_value<J>(Bs, nr, nr, k, BtB, xv, yv, lzw, lzw + a.rmax, lzw + a.rmax + 2 * (LZ_STEPS + 1), red);
+            // P^2 goes to Bs once B^T B is formed (B is no longer read then)
+            const double smax = top_singular_value<J>(Bs, nr, k, BtB, Psq, Bs, xv, yv, red);
             if (tid == 0) {
                 s_sin = smax;
                 s_measure = smax;

@@ -136,11 +136,19 @@ __device__ __forceinline__ double acc_read(const double *slot) {
     }
 }
 
+// Index of tile (ti, tj), ti <= tj, in the row-major enumeration of the
+// upper triangle of a tb x tb tile grid (the order tile_of decodes).
+__host__ __device__ inline size_t tri_tile(int ti, int tj, int tb) {
+    return (size_t)ti * tb - (size_t)ti * (ti - 1) / 2 + (size_t)(tj - ti);
+}
+
 // acc[p][q] += sum_i X[p][i] Y[q][i] over the bm rows of a slab (X, Y
 // column-major with leading dimension ld; p < na, q < nb).  Tiles of 4x4
 // outputs over 4-row chunks; tiles with ti > tj skipped when sym.  acc has
-// leading dimension ldacc (slots as in acc_add); red holds blockDim*16 T.
-// Ends with a barrier.
+// leading dimension ldacc (slots as in acc_add), or, when sym, holds the
+// computed tiles one after another (tile t of the upper triangle of the
+// ((nb + 3) / 4)-wide tile grid at acc + 16 t, row-major inside the tile);
+// red holds blockDim*16 T.  Ends with a barrier.
 // Tile t of the output grid: row-major over ta x tb tiles, or over the upper
 // triangle (ti <= tj) of a tb x tb grid when sym.
 __device__ __forceinline__ void tile_of(int t, int tb, bool sym, int &ti, int &tj) {
@@ -191,7 +199,9 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc_add(&acc[(4 * ti + u) * ldacc + 4 * tj + v], a[u * 4 + v]);
+                for (int v = 0; v < 4; ++v)
+                    acc_add(sym ? &acc[(size_t)tile * 16 + u * 4 + v] : &acc[(4 * ti + u) * ldacc + 4 * tj + v],
+                            a[u * 4 + v]);
         }
         __syncthreads();
         return;
@@ -227,7 +237,7 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
         tile_of(t2, tb, sym, i2, j2);
         T s = (T)0;
         for (int g2 = 0; g2 < RG; ++g2) s += red[(g2 * nT + t2) * 16 + uv];
-        acc_add(&acc[(4 * i2 + (uv >> 2)) * ldacc + 4 * j2 + (uv & 3)], s);
+        acc_add(sym ? &acc[(size_t)t2 * 16 + uv] : &acc[(4 * i2 + (uv >> 2)) * ldacc + 4 * j2 + (uv & 3)], s);
     }
     __syncthreads();
 }
@@ -271,7 +281,7 @@ __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, i
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
-                    acc[(4 * ti + u) * ldacc + 4 * tj + v] += (double)hi[u * 4 + v] + (double)lo[u * 4 + v];
+                    acc[tri_tile(ti, tj, ta) * 16 + u * 4 + v] += (double)hi[u * 4 + v] + (double)lo[u * 4 + v];
         } else {
             double a[16];
 #pragma unroll
@@ -292,7 +302,7 @@ __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, i
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[(4 * ti + u) * ldacc + 4 * tj + v] += a[u * 4 + v];
+                for (int v = 0; v < 4; ++v) acc[tri_tile(ti, tj, ta) * 16 + u * 4 + v] += a[u * 4 + v];
         }
     }
     __syncthreads();
@@ -339,27 +349,32 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
 }
 
 struct SmemPlan {
-    int ld;          // slab leading dimension (bm + pad)
+    int ld;          // slab leading dimension (= bm; the slabs are swizzled, not padded)
     int r4, c4;
     size_t buf;      // one slab buffer (r4 + c4 columns), elements
-    size_t ws;       // W buffer, elements
-    size_t s1, s2, s3;
-    size_t acc1, acc2;   // doubles
+    size_t ws;       // W buffer, elements (QR2 pass)
+    size_t s1, s2, s3;   // coefficient tiles, elements
+    size_t acc1, acc2;   // FP64 accumulators (doubles)
 };
 
-__host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm) {
+// Shared-memory layout of one pass: only what that kind uses.
+//   PROJ    acc1 = P (r4 x c4)
+//   CGS     S1 = P (r4 x c4); acc1 = P2 (r4 x c4); acc2 = Z^T Z (upper tiles)
+//   QR2     W slab; S1 = P, S2 = P2 (r4 x c4), S3 = M1 (c4 x c4); acc2 = W^T W (upper tiles)
+//   UPDATE  S1 = X (r4 x r4), S2 = Y (c4 x r4)
+__host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm, int kind) {
     SmemPlan p;
     p.ld = bm;
     p.r4 = round4(rmax);
     p.c4 = round4(cmax);
+    const size_t tb = (size_t)p.c4 / 4, tri = tb * (tb + 1) / 2 * 16;
     p.buf = (size_t)(p.r4 + p.c4) * p.ld;
-    p.ws = (size_t)p.c4 * p.ld;
-    // S1: P (r x g) or X (r x rn); S2: P2 (r x g) or Y (g x rn); S3: M1 (g x g)
-    p.s1 = (size_t)p.r4 * (p.c4 > p.r4 ? p.c4 : p.r4);
-    p.s2 = (size_t)p.c4 * p.r4;
-    p.s3 = (size_t)p.c4 * p.c4;
-    p.acc1 = (size_t)p.r4 * p.c4;
-    p.acc2 = (size_t)p.c4 * p.c4;
+    p.ws = kind == TALL_QR2 ? (size_t)p.c4 * p.ld : 0;
+    p.s1 = kind == TALL_CGS || kind == TALL_QR2 ? (size_t)p.r4 * p.c4 : (kind == TALL_UPDATE ? (size_t)p.r4 * p.r4 : 0);
+    p.s2 = kind == TALL_QR2 || kind == TALL_UPDATE ? (size_t)p.c4 * p.r4 : 0;
+    p.s3 = kind == TALL_QR2 ? (size_t)p.c4 * p.c4 : 0;
+    p.acc1 = kind == TALL_PROJ || kind == TALL_CGS ? (size_t)p.r4 * p.c4 : 0;
+    p.acc2 = kind == TALL_CGS || kind == TALL_QR2 ? tri : 0;
     return p;
 }
 
@@ -500,7 +515,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     if (a.cond && !st->robust) return;
     const int r = st->r_cur, g = st->g, rn = st->r_new;
     const int bm = a.bm;
-    const SmemPlan L = smem_plan(a.rmax, a.cmax, bm);
+    const SmemPlan L = smem_plan(a.rmax, a.cmax, bm, KIND);
     const int ld = L.ld, msk = sw_mask(bm);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf0 = reinterpret_cast<T *>(smem_raw);
@@ -567,6 +582,10 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         for (int e = tid; e < (int)L.acc1; e += bd) acc1[e] = 0.0;
         for (int e = tid; e < (int)L.acc2; e += bd) acc2[e] = 0.0;
     }
+    const int tbg = (g + 3) >> 2;   // tile columns of this round's Grams (tile-major acc2)
+    auto acc2_at = [&](int p, int q) {  // slot of entry (p, q), p <= q, of a symmetric Gram
+        return &acc2[tri_tile(p >> 2, q >> 2, tbg) * 16 + (p & 3) * 4 + (q & 3)];
+    };
 
     const int64_t step = (int64_t)gridDim.x * bm;
     int64_t i0 = (int64_t)blockIdx.x * bm;
@@ -705,12 +724,12 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         for (int e = tid; e < g * g; e += bd) {
             const int p = e / g, q = e - p * g;
             // the compensated Gram of the rerun keeps FP64 running sums
-            if (p <= q) outG[p * a.cmax + q] = a.cond ? acc2[p * L.c4 + q] : acc_read<T>(&acc2[p * L.c4 + q]);
+            if (p <= q) outG[p * a.cmax + q] = a.cond ? *acc2_at(p, q) : acc_read<T>(acc2_at(p, q));
         }
     } else {
         for (int e = tid; e < g * g; e += bd) {
             const int p = e / g, q = e - p * g;
-            if (p <= q) out[p * a.cmax + q] = acc_read<T>(&acc2[p * L.c4 + q]);
+            if (p <= q) out[p * a.cmax + q] = acc_read<T>(acc2_at(p, q));
         }
     }
     if (a.defer) return;   // summed by k_sum_parts
@@ -826,10 +845,14 @@ __global__ void __launch_bounds__(256) k_sign_dots(const T *U, int64_t m, int64_
 }
 
 template <typename T, int KIND>
-pod_status launch_kind(const TallArgs<T> &a, const TallPlan &plan, cudaStream_t st) {
-    POD_CUDA_TRY(cudaFuncSetAttribute(k_tall<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)plan.smem));
-    k_tall<T, KIND><<<plan.grid, TALL_THREADS, plan.smem, st>>>(a);
+pod_status launch_kind(const TallArgs<T> &a0, const TallPlan &plan, cudaStream_t st) {
+    // each kind has its own slab height and shared-memory layout
+    TallArgs<T> a = a0;
+    a.bm = plan.bm_k[KIND];
+    if (!plan.wide_k[KIND]) a.gscratch = nullptr;
+    const size_t smem = plan.smem_k[KIND];
+    POD_CUDA_TRY(cudaFuncSetAttribute(k_tall<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tall<T, KIND><<<plan.grid, TALL_THREADS, smem, st>>>(a);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }
@@ -848,42 +871,61 @@ pod_status launch_sum_parts(const SumParts &a, int cols_cap, cudaStream_t s) {
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
     TallPlan p{};
     const bool f32 = dtype == POD_F32;
-    auto bytes_for = [&](int bm) {
-        SmemPlan L = smem_plan(rmax, cmax, bm);
+    auto bytes_for = [&](int bm, int kind) {
+        SmemPlan L = smem_plan(rmax, cmax, bm, kind);
         return f32 ? smem_bytes<float>(L) : smem_bytes<double>(L);
     };
-    // prefer two resident CTAs per SM (16 warps), then the largest slab
-    int bm = 0, per_sm = 2;
-    for (int b = 128; b >= 32 && !bm; b >>= 1)
-        if (bytes_for(b) <= 110 * 1024) bm = b;
-    if (!bm) {
-        per_sm = 1;
-        for (int b = 128; b >= 16 && !bm; b >>= 1)
-            if (bytes_for(b) <= 200 * 1024) bm = b;
+    auto wide_for = [&](int bm, int kind) {
+        SmemPlan L = smem_plan(rmax, cmax, bm, kind);
+        return f32 ? smem_bytes_wide<float>(L) : smem_bytes_wide<double>(L);
+    };
+    // two resident CTAs per SM (16 warps) when every kind fits in 110 KB with
+    // slabs of at least 32 rows; else one CTA per SM, each kind with the
+    // tallest slab whose layout fits in 200 KB; a kind that does not fit even
+    // with 16-row slabs keeps its coefficient tiles and accumulators in global
+    // scratch (wide)
+    int per_sm = 2;
+    for (int k = 0; k < 4 && per_sm == 2; ++k) {
+        int bm = 0;
+        for (int b = 128; b >= 32 && !bm; b >>= 1)
+            if (bytes_for(b, k) <= 110 * 1024) bm = b;
+        if (!bm) per_sm = 1;
+        p.bm_k[k] = bm;
+        p.smem_k[k] = bm ? bytes_for(bm, k) : 0;
     }
-    if (bm) {
-        p.bm = bm;
-        p.smem = bytes_for(bm);
-    } else {
-        // wide: coefficient tiles and accumulators in global scratch
-        auto wide_for = [&](int b) {
-            SmemPlan L = smem_plan(rmax, cmax, b);
-            return f32 ? smem_bytes_wide<float>(L) : smem_bytes_wide<double>(L);
-        };
-        per_sm = 1;
-        bm = 16;
-        for (int b = 64; b >= 16; b >>= 1)
-            if (wide_for(b) <= 200 * 1024) {
-                bm = b;
-                break;
+    if (per_sm == 1) {
+        for (int k = 0; k < 4; ++k) {
+            int bm = 0;
+            for (int b = 128; b >= 16 && !bm; b >>= 1)
+                if (bytes_for(b, k) <= 200 * 1024) bm = b;
+            p.wide_k[k] = 0;
+            if (bm) {
+                p.bm_k[k] = bm;
+                p.smem_k[k] = bytes_for(bm, k);
+                continue;
             }
-        SmemPlan L = smem_plan(rmax, cmax, bm);
-        p.bm = bm;
-        p.smem = wide_for(bm);
-        p.wide = 1;
-        p.gstride = (int64_t)(f32 ? gscratch_bytes<float>(L) : gscratch_bytes<double>(L));
+            bm = 16;
+            for (int b = 64; b >= 16; b >>= 1)
+                if (wide_for(b, k) <= 200 * 1024) {
+                    bm = b;
+                    break;
+                }
+            SmemPlan L = smem_plan(rmax, cmax, bm, k);
+            p.bm_k[k] = bm;
+            p.smem_k[k] = wide_for(bm, k);
+            p.wide_k[k] = 1;
+            const int64_t gs = (int64_t)(f32 ? gscratch_bytes<float>(L) : gscratch_bytes<double>(L));
+            if (gs > p.gstride) p.gstride = gs;
+        }
     }
-    const int64_t slabs = (m + bm - 1) / bm;
+    p.bm = p.bm_k[TALL_PROJ];
+    p.smem = 0;
+    p.wide = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (p.smem_k[k] > p.smem) p.smem = p.smem_k[k];
+        p.wide |= p.wide_k[k];
+    }
+    const int64_t slabs = (m + 15) / 16;
     int64_t grid = (int64_t)per_sm * num_sms;
     if (grid > slabs) grid = slabs;
     if (grid < 1) grid = 1;
