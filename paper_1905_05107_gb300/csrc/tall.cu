@@ -691,6 +691,9 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         __syncthreads();
     }
     cp_async_wait<0>();
+    // a CTA whose first slab lies beyond m never entered the loop: its
+    // accumulators were zeroed by all threads with no barrier since
+    __syncthreads();
     if (KIND == TALL_UPDATE) {
         if (a.finish) {
             // end of the round, by the last CTA to finish its rows (every CTA
@@ -925,7 +928,12 @@ TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
         if (p.smem_k[k] > p.smem) p.smem = p.smem_k[k];
         p.wide |= p.wide_k[k];
     }
-    const int64_t slabs = (m + 15) / 16;
+    // CTAs: at most one per slab of the tallest kind, so that every CTA of
+    // every kind has rows (idle CTAs would only add zero partials)
+    int bmx = 16;
+    for (int k = 0; k < 4; ++k)
+        if (p.bm_k[k] > bmx) bmx = p.bm_k[k];
+    const int64_t slabs = (m + bmx - 1) / bmx;
     int64_t grid = (int64_t)per_sm * num_sms;
     if (grid > slabs) grid = slabs;
     if (grid < 1) grid = 1;
