@@ -74,6 +74,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # profiling runs: the headline workload alone (no flow, precision,
+    # differentiable or CPU legs), optionally at reduced m x n; the timed
+    # steps sit inside the NVTX range "timed" (ncu --nvtx --nvtx-include timed/)
+    ap.add_argument("--only-head", action="store_true")
+    ap.add_argument("--m", type=int, default=0)
+    ap.add_argument("--n", type=int, default=0)
     return ap.parse_args()
 
 
@@ -174,8 +180,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make_head():
+def make_head(m=0, n=0):
     from paper_1905_05107_gb300 import synth
+    if m or n:
+        return synth.make_precision_c3(m=m or 1_000_000, n=n or 4000)
     return synth.make_precision_c3()      # (m, n) Fortran-ordered float32
 
 
@@ -330,10 +338,12 @@ def time_problem(torch, pod, A_np, w, steps, warmup, dev, world, detail):
         l0, _ = ctx.counters()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(steps):
             U, sigma, _ = step()
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         l1, _ = ctx.counters()
         out["clocks"] = clocks.stop() if clocks else None
@@ -591,28 +601,33 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     from paper_1905_05107_gb300 import build, pod
     build.build()
-    A_np = make_head()
+    A_np = make_head(args.m, args.n)
     m, n = A_np.shape
     k = HEAD["k"]
-    t = time_problem(torch, pod, A_np, HEAD, args.steps, args.warmup, dev, world, detail=True)
+    head = dict(HEAD)
+    if (m, n) != (1_000_000, 4000):
+        head["workload"] = "planted-%dx%d-f32" % (m, n)
+    t = time_problem(torch, pod, A_np, head, args.steps, args.warmup, dev, world, detail=True)
     hbm, bf16, bf16_sus, peak_kind = load_peaks()
     roof = roofline_of(t, m, n, k, hbm, bf16, tc_proj=True)
     roof["peak_source"] = roof.get("peak_source", "%s: MEASURED_PEAKS.json hbm_gbs" % peak_kind)
     roof["tensor_peak_source"] = ("%s: MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio (1.1 / 2.25)"
                                   % peak_kind)
     core_phase = np.mean(np.array(t["core_cyc"], dtype=np.float64), axis=0).tolist()
-    # the FP32 flow workload beside it
-    F_np = make_flow()
-    tf = time_problem(torch, pod, F_np, FLOW, args.steps, args.warmup, dev, world, detail=False)
-    flow = {"workload": FLOW["workload"], "m": int(F_np.shape[0]), "n": int(F_np.shape[1]), "k": FLOW["k"],
-            "c": FLOW["c"], "rounds": tf["rounds"], "ms_per_step": tf["ms"], "e2e_ms": tf["ms_e2e"],
-            "gpu_launches": int(tf["launches"])}
-    del F_np
-    forms = precision_forms(torch, pod, A_np, HEAD, dev) if world == 1 else None
-    diff = differentiable_form(torch, pod, dev) if world == 1 else None
+    flow, forms, diff = None, None, None
+    if not args.only_head:
+        # the FP32 flow workload beside it
+        F_np = make_flow()
+        tf = time_problem(torch, pod, F_np, FLOW, args.steps, args.warmup, dev, world, detail=False)
+        flow = {"workload": FLOW["workload"], "m": int(F_np.shape[0]), "n": int(F_np.shape[1]), "k": FLOW["k"],
+                "c": FLOW["c"], "rounds": tf["rounds"], "ms_per_step": tf["ms"], "e2e_ms": tf["ms_e2e"],
+                "gpu_launches": int(tf["launches"])}
+        del F_np
+        forms = precision_forms(torch, pod, A_np, head, dev) if world == 1 else None
+        diff = differentiable_form(torch, pod, dev) if world == 1 else None
     cpu, acc = None, None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        secs, ref = oracle_full(A_np, HEAD)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.only_head:
+        secs, ref = oracle_full(A_np, head)
         cpu = {"value": secs, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
                "sample": "the whole problem once: FP64 NumPy/LAPACK oracle (Algorithm 1, %d rounds, refinement) "
                          "on the host cores" % len(ref.trace)}
@@ -629,7 +644,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": t["ms"] / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t["ms"], "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": HEAD["workload"], "m": int(m), "n": int(n), "k": k, "c": HEAD["c"],
+                "config": {"workload": head["workload"], "m": int(m), "n": int(n), "k": k, "c": HEAD["c"],
                            "tol": HEAD["tol"], "rounds": t["rounds"], "strategy": "L2N round 0, UNF after",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "contractions": "A^T U on tcgen05 tensor cores, split-TF32 (3 products)",
