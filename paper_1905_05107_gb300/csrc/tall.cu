@@ -142,13 +142,24 @@ __host__ __device__ inline size_t tri_tile(int ti, int tj, int tb) {
     return (size_t)ti * tb - (size_t)ti * (ti - 1) / 2 + (size_t)(tj - ti);
 }
 
+// Accumulator slot of output (p, q) of an na x nb product (sym: p <= q of an
+// nb x nb Gram).  Outputs are grouped in 4x4 tiles (row-major over the tile
+// grid, or over its upper triangle when sym) and stored element-major: slot
+// e * nT + tile, e = 4 (p mod 4) + (q mod 4), nT = the number of tiles, so
+// the threads of a warp, which hold consecutive tiles, touch consecutive
+// slots.
+__device__ __forceinline__ double *gram_slot(double *acc, int na, int nb, bool sym, int p, int q) {
+    const int tb = (nb + 3) >> 2;
+    const int nT = sym ? tb * (tb + 1) / 2 : ((na + 3) >> 2) * tb;
+    const size_t tile = sym ? tri_tile(p >> 2, q >> 2, tb) : (size_t)(p >> 2) * tb + (q >> 2);
+    return acc + (size_t)((p & 3) * 4 + (q & 3)) * nT + tile;
+}
+
 // acc[p][q] += sum_i X[p][i] Y[q][i] over the bm rows of a slab (X, Y
 // column-major with leading dimension ld; p < na, q < nb).  Tiles of 4x4
-// outputs over 4-row chunks; tiles with ti > tj skipped when sym.  acc has
-// leading dimension ldacc (slots as in acc_add), or, when sym, holds the
-// computed tiles one after another (tile t of the upper triangle of the
-// ((nb + 3) / 4)-wide tile grid at acc + 16 t, row-major inside the tile);
-// red holds blockDim*16 T.  Ends with a barrier.
+// outputs over 4-row chunks; tiles with ti > tj skipped when sym.  acc slots
+// (as in acc_add) laid out as gram_slot gives; red holds blockDim*16 T.  Ends
+// with a barrier.
 // Tile t of the output grid: row-major over ta x tb tiles, or over the upper
 // triangle (ti <= tj) of a tb x tb grid when sym.
 __device__ __forceinline__ void tile_of(int t, int tb, bool sym, int &ti, int &tj) {
@@ -168,7 +179,7 @@ __device__ __forceinline__ void tile_of(int t, int tb, bool sym, int &ti, int &t
 
 template <typename T>
 __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm, bool sym, double *acc,
-                         int ldacc, T *red) {
+                         T *red) {
     const int tid = threadIdx.x, bd = blockDim.x;
     const int msk = sw_mask(bm);
     const int ta = (na + 3) >> 2, tb = (nb + 3) >> 2;
@@ -199,9 +210,7 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    acc_add(sym ? &acc[(size_t)tile * 16 + u * 4 + v] : &acc[(4 * ti + u) * ldacc + 4 * tj + v],
-                            a[u * 4 + v]);
+                for (int v = 0; v < 4; ++v) acc_add(&acc[(size_t)(u * 4 + v) * nT + tile], a[u * 4 + v]);
         }
         __syncthreads();
         return;
@@ -228,16 +237,14 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
                     for (int w = 0; w < 4; ++w) a[u * 4 + v] = fma(x[u][w], y[v][w], a[u * 4 + v]);
         }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) red[(grp * nT + tile) * 16 + e] = a[e];
+        for (int e = 0; e < 16; ++e) red[(e * RG + grp) * nT + tile] = a[e];
     }
     __syncthreads();
     for (int e = tid; e < nT * 16; e += bd) {
-        const int t2 = e >> 4, uv = e & 15;
-        int i2, j2;
-        tile_of(t2, tb, sym, i2, j2);
+        const int uv = e / nT, t2 = e - uv * nT;
         T s = (T)0;
-        for (int g2 = 0; g2 < RG; ++g2) s += red[(g2 * nT + t2) * 16 + uv];
-        acc_add(sym ? &acc[(size_t)t2 * 16 + uv] : &acc[(4 * i2 + (uv >> 2)) * ldacc + 4 * j2 + (uv & 3)], s);
+        for (int g2 = 0; g2 < RG; ++g2) s += red[(uv * RG + g2) * nT + t2];
+        acc_add(&acc[e], s);
     }
     __syncthreads();
 }
@@ -246,10 +253,11 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 // (TwoProduct) and summed with TwoSum: the tile sums carry ~44 bits before the
 // FP64 flush.  Used for the first CholeskyQR Gram when the plain FP32 one
 // proved too inexact (ill-conditioned residual blocks).  Its acc slots are
-// plain doubles (FP64 running sums).  Ends with a barrier.
+// plain doubles (FP64 running sums), laid out as gram_slot gives for sym.
+// Ends with a barrier.
 template <typename T>
-__device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, int ldacc) {
-    const int ta = (na + 3) >> 2, nT = ta * ta, chunks = bm >> 2;
+__device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc) {
+    const int ta = (na + 3) >> 2, nT = ta * ta, nTs = ta * (ta + 1) / 2, chunks = bm >> 2;
     const int msk = sw_mask(bm);
     for (int tile = threadIdx.x; tile < nT; tile += blockDim.x) {
         const int ti = tile / ta, tj = tile - ti * ta;
@@ -281,7 +289,7 @@ __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, i
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
-                    acc[tri_tile(ti, tj, ta) * 16 + u * 4 + v] += (double)hi[u * 4 + v] + (double)lo[u * 4 + v];
+                    acc[(size_t)(u * 4 + v) * nTs + tri_tile(ti, tj, ta)] += (double)hi[u * 4 + v] + (double)lo[u * 4 + v];
         } else {
             double a[16];
 #pragma unroll
@@ -302,7 +310,7 @@ __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc, i
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[tri_tile(ti, tj, ta) * 16 + u * 4 + v] += a[u * 4 + v];
+                for (int v = 0; v < 4; ++v) acc[(size_t)(u * 4 + v) * nTs + tri_tile(ti, tj, ta)] += a[u * 4 + v];
         }
     }
     __syncthreads();
@@ -582,10 +590,6 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         for (int e = tid; e < (int)L.acc1; e += bd) acc1[e] = 0.0;
         for (int e = tid; e < (int)L.acc2; e += bd) acc2[e] = 0.0;
     }
-    const int tbg = (g + 3) >> 2;   // tile columns of this round's Grams (tile-major acc2)
-    auto acc2_at = [&](int p, int q) {  // slot of entry (p, q), p <= q, of a symmetric Gram
-        return &acc2[tri_tile(p >> 2, q >> 2, tbg) * 16 + (p & 3) * 4 + (q & 3)];
-    };
 
     const int64_t step = (int64_t)gridDim.x * bm;
     int64_t i0 = (int64_t)blockIdx.x * bm;
@@ -608,7 +612,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         cp_async_wait<1>();
         __syncthreads();
         if (KIND == TALL_PROJ) {
-            gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, L.c4, red);
+            gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, red);
         } else if (KIND == TALL_CGS) {
             if (r > 0) {
                 rowspace_tiles<T>(bm, g, Us, r, S1, g4, Us, 0, S2, g4, ld, false,
@@ -624,10 +628,10 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                                       }
                                   });
                 __syncthreads();
-                gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, L.c4, red);
+                gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, red);
             }
-            if (a.cond) gram_acc_comp<T>(Cs, g, ld, bm, acc2, L.c4);
-            else gram_acc<T>(Cs, g, Cs, g, ld, bm, true, acc2, L.c4, red);
+            if (a.cond) gram_acc_comp<T>(Cs, g, ld, bm, acc2);
+            else gram_acc<T>(Cs, g, Cs, g, ld, bm, true, acc2, red);
         } else if (KIND == TALL_QR2) {
             if (r > 0) {
                 rowspace_tiles<T>(bm, g, Us, r, S1, g4, Us, r, S2, g4, ld, false,
@@ -665,7 +669,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
                     if (i < nrow) a.Wout[(int64_t)j * a.ldw + i0 + i] = Ws[(size_t)j * ld + swz(j, i, msk)];
                 }
             }
-            gram_acc<T>(Ws, g, Ws, g, ld, bm, true, acc2, L.c4, red);
+            gram_acc<T>(Ws, g, Ws, g, ld, bm, true, acc2, red);
         } else {
             const int64_t rows_left = a.m - i0;
             rowspace_tiles<T>(bm, rn, Us, r, S1, rn4, Cs, g, S2, rn4, ld, false,
@@ -716,23 +720,24 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     if (KIND == TALL_PROJ) {
         for (int e = tid; e < r * g; e += bd) {
             const int l = e / g, j = e - l * g;
-            out[l * a.cmax + j] = acc_read<T>(&acc1[l * L.c4 + j]);
+            out[l * a.cmax + j] = acc_read<T>(gram_slot(acc1, r, g, false, l, j));
         }
     } else if (KIND == TALL_CGS) {
         for (int e = tid; e < r * g; e += bd) {
             const int l = e / g, j = e - l * g;
-            out[l * a.cmax + j] = acc_read<T>(&acc1[l * L.c4 + j]);
+            out[l * a.cmax + j] = acc_read<T>(gram_slot(acc1, r, g, false, l, j));
         }
         double *outG = out + (int64_t)a.rmax * a.cmax;
         for (int e = tid; e < g * g; e += bd) {
             const int p = e / g, q = e - p * g;
             // the compensated Gram of the rerun keeps FP64 running sums
-            if (p <= q) outG[p * a.cmax + q] = a.cond ? *acc2_at(p, q) : acc_read<T>(acc2_at(p, q));
+            if (p <= q) outG[p * a.cmax + q] = a.cond ? *gram_slot(acc2, g, g, true, p, q)
+                                                       : acc_read<T>(gram_slot(acc2, g, g, true, p, q));
         }
     } else {
         for (int e = tid; e < g * g; e += bd) {
             const int p = e / g, q = e - p * g;
-            if (p <= q) out[p * a.cmax + q] = acc_read<T>(acc2_at(p, q));
+            if (p <= q) out[p * a.cmax + q] = acc_read<T>(gram_slot(acc2, g, g, true, p, q));
         }
     }
     if (a.defer) return;   // summed by k_sum_parts
@@ -800,7 +805,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_atu(AtuArgs<T> a, int nb, int 
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            gram_acc<T>(As, ncols, As + (size_t)nb4 * ld, r, ld, bm, false, acc, r4, red);
+            gram_acc<T>(As, ncols, As + (size_t)nb4 * ld, r, ld, bm, false, acc, red);
         }
         cp_async_wait<0>();
     }
@@ -809,7 +814,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_atu(AtuArgs<T> a, int nb, int 
     double *out = a.part + (int64_t)blockIdx.y * a.n * a.rmax;
     for (int e = tid; e < ncols * r; e += bd) {
         const int l = e / ncols, c = e - l * ncols;
-        out[(int64_t)l * a.n + j0 + c] = acc_read<T>(&acc[c * r4 + l]);
+        out[(int64_t)l * a.n + j0 + c] = acc_read<T>(gram_slot(acc, ncols, r, false, c, l));
     }
     // the last of the `split` CTAs of this column block sums them
     __threadfence();
