@@ -537,11 +537,17 @@ static pod_status enqueue_round(pod_ctx *c) {
     sm.wq = 1;
     POD_TRY(launch_small_chol(sm, s));
     mark(c);
-    ta.part_stride = (int64_t)c->cmax * c->cmax;
-    ta.out = c->G2;
-    POD_TRY(launch_tall<T>(TALL_QR2, ta, c->plan, s));
+    // QR2 reads the Z that the CGS pass stored in Wbuf and writes W over it
+    TallArgs<T> qa = ta;
+    qa.A = (const T *)c->Wbuf;
+    qa.idx = nullptr;
+    qa.lda = c->p.m;
+    qa.vec = (c->p.m * (int64_t)sizeof(T)) % 16 == 0;
+    qa.part_stride = (int64_t)c->cmax * c->cmax;
+    qa.out = c->G2;
+    POD_TRY(launch_tall<T>(TALL_QR2, qa, c->plan, s));
     mark(c);
-    sp.stride = ta.part_stride;
+    sp.stride = qa.part_stride;
     sp.out = c->G2;
     sp.rect = 0;
     sp.tri = 1;
@@ -566,9 +572,10 @@ static pod_status enqueue_round(pod_ctx *c) {
         mark(c);
         POD_TRY(launch_small_chol(sr, s));
         mark(c);
-        tr.part_stride = (int64_t)c->cmax * c->cmax;
-        tr.out = c->G2;
-        POD_TRY(launch_tall<T>(TALL_QR2, tr, c->plan, s));
+        TallArgs<T> qr = qa;   // reads the Z the rerun of CGS stored again
+        qr.cond = 1;
+        qr.defer = 0;
+        POD_TRY(launch_tall<T>(TALL_QR2, qr, c->plan, s));
         mark(c);
     }
     POD_TRY(launch_core(sm, s));

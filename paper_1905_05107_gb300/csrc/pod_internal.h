@@ -69,8 +69,9 @@ struct TallArgs {
     int cond;               // 1: run only when st->robust is set (and then with a
                             // compensated Gram in the CGS pass); the QR2 pass with
                             // cond = 0 sets st->robust from its G2
-    T *Wout;                // QR2 pass: W = (Z - U P2) M1 stored here (m x g, ld ldw),
-    int64_t ldw;            // the block the UPDATE pass then combines (or null)
+    T *Wout;                // CGS pass: Z = C - U P stored here; QR2 pass (reading that Z
+    int64_t ldw;            // as its C operand): W = (Z - U P2) M1 stored over it, the block
+                            // the UPDATE pass then combines (m x g, ld ldw; or null)
     int defer;              // 1: write this CTA's partial and return; k_sum_parts sums
     unsigned *finish;       // UPDATE of a round: arrival counter; the last CTA ends the
                             // round (r_cur <- r_new, t + 1, the stop decision), or null

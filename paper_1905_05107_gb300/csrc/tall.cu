@@ -1,8 +1,9 @@
 // Tall-skinny passes of BLOCK MERGE (Algorithm 2) over the m rows:
 //   TALL_PROJ   : P  = U^T C                              (U_1^T U_2, Eq. 8)
-//   TALL_CGS    : Z  = C - U P;  P2 = U^T Z;  G = Z^T Z    (U_t, second projection)
-//   TALL_QR2    : W  = (C - U P - U P2) M1;  G2 = W^T W     (second CholeskyQR pass;
-//                 W is stored)
+//   TALL_CGS    : Z  = C - U P;  P2 = U^T Z;  G = Z^T Z    (U_t, second projection;
+//                 Z is stored)
+//   TALL_QR2    : W  = (Z - U P2) M1;  G2 = W^T W          (second CholeskyQR pass;
+//                 W is stored over Z)
 //   TALL_UPDATE : U <- U X + W Y                          (U = [U_1 U_o] U_E, truncated;
 //                 U_o = W R2^{-1}; the ICRS row stage combines C instead of W)
 // plus Y = A^T U (closing refinement of Algorithm 1, ORT probabilities) and
@@ -368,7 +369,7 @@ struct SmemPlan {
 // Shared-memory layout of one pass: only what that kind uses.
 //   PROJ    acc1 = P (r4 x c4)
 //   CGS     S1 = P (r4 x c4); acc1 = P2 (r4 x c4); acc2 = Z^T Z (upper tiles)
-//   QR2     W slab; S1 = P, S2 = P2 (r4 x c4), S3 = M1 (c4 x c4); acc2 = W^T W (upper tiles)
+//   QR2     W slab; S2 = P2 (r4 x c4), S3 = M1 (c4 x c4); acc2 = W^T W (upper tiles)
 //   UPDATE  S1 = X (r4 x r4), S2 = Y (c4 x r4)
 __host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm, int kind) {
     SmemPlan p;
@@ -378,7 +379,7 @@ __host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm, int ki
     const size_t tb = (size_t)p.c4 / 4, tri = tb * (tb + 1) / 2 * 16;
     p.buf = (size_t)(p.r4 + p.c4) * p.ld;
     p.ws = kind == TALL_QR2 ? (size_t)p.c4 * p.ld : 0;
-    p.s1 = kind == TALL_CGS || kind == TALL_QR2 ? (size_t)p.r4 * p.c4 : (kind == TALL_UPDATE ? (size_t)p.r4 * p.r4 : 0);
+    p.s1 = kind == TALL_CGS ? (size_t)p.r4 * p.c4 : (kind == TALL_UPDATE ? (size_t)p.r4 * p.r4 : 0);
     p.s2 = kind == TALL_QR2 || kind == TALL_UPDATE ? (size_t)p.c4 * p.r4 : 0;
     p.s3 = kind == TALL_QR2 ? (size_t)p.c4 * p.c4 : 0;
     p.acc1 = kind == TALL_PROJ || kind == TALL_CGS ? (size_t)p.r4 * p.c4 : 0;
@@ -565,8 +566,8 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
     if (KIND == TALL_CGS || KIND == TALL_QR2) {
         for (int e = tid; e < r4 * g4; e += bd) {
             const int l = e / g4, j = e - l * g4;
-            S1[e] = (l < r && j < g) ? (T)a.P[l * a.cmax + j] : (T)0;
-            if (KIND == TALL_QR2) S2[e] = (l < r && j < g) ? (T)a.P2[l * a.cmax + j] : (T)0;
+            if (KIND == TALL_CGS) S1[e] = (l < r && j < g) ? (T)a.P[l * a.cmax + j] : (T)0;
+            else S2[e] = (l < r && j < g) ? (T)a.P2[l * a.cmax + j] : (T)0;
         }
     }
     if (KIND == TALL_QR2) {
@@ -614,7 +615,11 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         if (KIND == TALL_PROJ) {
             gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, red);
         } else if (KIND == TALL_CGS) {
+            // Z is also stored (a.Wout) for the QR2 pass, which then only
+            // removes U P2
+            const int64_t rows_left = a.m - i0;
             if (r > 0) {
+                const bool zvec = (a.ldw * (int64_t)sizeof(T)) % 16 == 0;
                 rowspace_tiles<T>(bm, g, Us, r, S1, g4, Us, 0, S2, g4, ld, false,
                                   [&](int rc, int cj, T (&a1)[4][4], T (&)[4][4]) {
 #pragma unroll
@@ -625,24 +630,41 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
 #pragma unroll
                                           for (int u = 0; u < 4; ++u) z[u] -= a1[u][v];
                                           sts4(p, z);
+                                          const int q = 4 * cj + v;
+                                          if (!a.Wout || q >= g) continue;
+                                          T *dst = a.Wout + (int64_t)q * a.ldw + i0 + 4 * rc;
+                                          if (zvec && rows_left >= 4 * rc + 4) {
+                                              sts4(dst, z);
+                                          } else {
+#pragma unroll
+                                              for (int u = 0; u < 4; ++u)
+                                                  if (4 * rc + u < rows_left) dst[u] = z[u];
+                                          }
                                       }
                                   });
                 __syncthreads();
                 gram_acc<T>(Us, r, Cs, g, ld, bm, false, acc1, red);
+            } else if (a.Wout) {
+                const int nrow = rows_left < bm ? (int)rows_left : bm;
+                for (int e = tid; e < g * bm; e += bd) {
+                    const int j = e / bm, i = e - j * bm;
+                    if (i < nrow) a.Wout[(int64_t)j * a.ldw + i0 + i] = Cs[(size_t)j * ld + swz(j, i, msk)];
+                }
             }
             if (a.cond) gram_acc_comp<T>(Cs, g, ld, bm, acc2);
             else gram_acc<T>(Cs, g, Cs, g, ld, bm, true, acc2, red);
         } else if (KIND == TALL_QR2) {
+            // the C operand is Z = C - U P as the CGS pass stored it
             if (r > 0) {
-                rowspace_tiles<T>(bm, g, Us, r, S1, g4, Us, r, S2, g4, ld, false,
-                                  [&](int rc, int cj, T (&a1)[4][4], T (&a2)[4][4]) {
+                rowspace_tiles<T>(bm, g, Us, r, S2, g4, Us, 0, S2, g4, ld, false,
+                                  [&](int rc, int cj, T (&a2)[4][4], T (&)[4][4]) {
 #pragma unroll
                                       for (int v = 0; v < 4; ++v) {
                                           T *p = Cs + (size_t)(4 * cj + v) * ld + ((rc ^ (cj & msk)) << 2);
                                           T z[4];
                                           lds4(p, z);
 #pragma unroll
-                                          for (int u = 0; u < 4; ++u) z[u] = (z[u] - a1[u][v]) - a2[u][v];
+                                          for (int u = 0; u < 4; ++u) z[u] -= a2[u][v];
                                           sts4(p, z);
                                       }
                                   });
