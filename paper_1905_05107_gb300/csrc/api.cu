@@ -998,7 +998,11 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
         return POD_EUNSUPPORTED;
     }
     const bool wide_core = core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) > 220 * 1024;
-    const bool wide_chol = small_chol_smem(c->cmax) > 220 * 1024;
+    // global scratch when one of the forms this context runs (plain, the
+    // compensated rerun) does not fit in shared memory
+    const size_t chol_bytes = small_chol_smem(c->cmax, p->dtype, 1) > small_chol_smem(c->cmax, p->dtype, 0)
+                                  ? small_chol_smem(c->cmax, p->dtype, 1) : small_chol_smem(c->cmax, p->dtype, 0);
+    const bool wide_chol = chol_bytes > 220 * 1024;
     const bool wide_refine = refine_gws_bytes(c->rmax) > 220 * 1024;
     c->jac_smem = wide_core && core_jacobi_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32) <= 200 * 1024;
     if (wide_core && (p->rows || p->block_trunc)) {
@@ -1090,7 +1094,7 @@ pod_status pod_init(pod_ctx **ctx_out, const pod_params *p, const void *A_dev, v
     if (p->keep_tape) ALLOC(c->tape_d, 1);
     if (c->plan.wide) ALLOC(c->tall_gs, (size_t)c->plan.grid * c->plan.gstride);
     if (wide_core) ALLOC(c->core_gs, core_smem_bytes(c->rmax, c->cmax, c->core_f64 ? POD_F64 : POD_F32));
-    if (wide_chol) ALLOC(c->chol_gs, small_chol_smem(c->cmax));
+    if (wide_chol) ALLOC(c->chol_gs, chol_bytes);
     if (wide_refine) ALLOC(c->refine_gs, refine_gws_bytes(c->rmax));
     {
         const TallPlan yp = tall_plan(POD_F64, n, rm, rm, c->sms);

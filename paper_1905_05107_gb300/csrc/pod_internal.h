@@ -375,7 +375,7 @@ pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s);
 pod_status launch_core(const SmallArgs &a, cudaStream_t s);
 size_t core_smem_bytes(int rmax, int cmax, int dtype);
 size_t core_jacobi_bytes(int rmax, int cmax, int dtype);   // shared memory of the Jacobi arrays alone
-size_t small_chol_smem(int cmax);
+size_t small_chol_smem(int cmax, int dtype, int cond);   // bytes of k_small_chol's work area
 
 
 // refinement QR(A^T U), SVD(R)

@@ -114,6 +114,36 @@ __device__ void tri_inv(const X *R, int ldr, int n, X *Mw, int ldw, X *M, int ld
     }
 }
 
+// As tri_inv, with M = R^{-1} written straight to the FP64 array out (ld
+// ldo; the whole n x n block, zeros below the diagonal and in the rows and
+// columns of dropped indices).
+template <typename X>
+__device__ void tri_inv_out(const X *R, int ldr, int n, X *Mw, int ldw, double *out, int ldo, X *dinv) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    for (int e = tid; e < n * n; e += bd) {
+        const int i = e / n, j = e % n;
+        Mw[i * ldw + j] = (i == j) ? XOps<X>::one() : XOps<X>::zero();
+        out[i * ldo + j] = 0.0;
+    }
+    for (int k = tid; k < n; k += bd) {
+        const X d = R[k * ldr + k];
+        dinv[k] = x_hi(d) != 0.f ? XOps<X>::one() / d : XOps<X>::zero();
+    }
+    const int NC = col_lanes(n, bd), RS = bd / NC;
+    const int jt = tid & (NC - 1), it = tid / NC;
+    __syncthreads();
+    for (int k = n - 1; k >= 0; --k) {
+        const X inv = dinv[k];
+        if (x_hi(inv) != 0.f && it < RS)
+            for (int j = k + jt; j < n; j += NC) {
+                const X mkj = Mw[k * ldw + j] * inv;
+                if (it == 0) out[k * ldo + j] = XOps<X>::to(mkj);
+                for (int i = it; i < k; i += RS) Mw[i * ldw + j] = Mw[i * ldw + j] - R[i * ldr + k] * mkj;
+            }
+        __syncthreads();
+    }
+}
+
 // C = A B for upper triangular A, B (all entries in parallel).
 template <typename X>
 __device__ void trmm_upper(const X *A, int lda, const X *B, int ldb, int n, X *C, int ldc) {
@@ -697,6 +727,23 @@ pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t
 // before use, so an FP32 inverse costs no accuracy: both errors are
 // O(u kappa)); X (double-float or FP64) in the compensated rerun and for FP64
 // data.  R1p, the inverse of the applied M1, is always formed in X.
+struct Chol1Layout {
+    size_t xc, x;      // one ld x ld array of XC / of X (16-byte multiples)
+    size_t main;       // the larger of 4 xc and 2 x
+    size_t vec;        // one length-ld X vector
+    size_t total;
+};
+__host__ __device__ inline Chol1Layout chol1_layout(int ld, int xs, int xcs) {
+    Chol1Layout L;
+    L.xc = al16x((size_t)ld * ld * xcs);
+    L.x = al16x((size_t)ld * ld * xs);
+    L.main = 4 * L.xc > 2 * L.x ? 4 * L.xc : 2 * L.x;
+    if (L.main < L.x) L.main = L.x;   // the column-norm squares (ld^2 doubles)
+    L.vec = al16x((size_t)ld * xs);
+    L.total = L.main + 2 * L.vec + 64;
+    return L;
+}
+
 template <typename X, typename XC>
 __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
     DevState *st = a.st;
@@ -705,27 +752,28 @@ __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
     const int r = st->r_cur, g = st->g, nc = r + g;
     const int ld = a.cmax;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Carve cv{a.gws_chol ? a.gws_chol : smem_raw};
-    X *W = cv.take<X>((size_t)ld * ld);
-    X *R = cv.take<X>((size_t)ld * ld);
-    X *Mw = cv.take<X>((size_t)ld * ld);
-    X *M = cv.take<X>((size_t)ld * ld);
+    // layout (chol1_layout): the XC stage's four ld x ld XC arrays, or the
+    // X stage's two ld x ld X arrays, over the same bytes; then dinv and the
+    // pivot floors
+    const Chol1Layout CL = chol1_layout(ld, (int)sizeof(X), (int)sizeof(XC));
+    unsigned char *base = a.gws_chol ? a.gws_chol : smem_raw;
+    XC *Wc = reinterpret_cast<XC *>(base), *Rc = reinterpret_cast<XC *>(base + CL.xc);
+    XC *Mwc = reinterpret_cast<XC *>(base + 2 * CL.xc), *Mc = reinterpret_cast<XC *>(base + 3 * CL.xc);
+    X *R = reinterpret_cast<X *>(base), *Mw = reinterpret_cast<X *>(base + CL.x);
+    X *dinv = reinterpret_cast<X *>(base + CL.main);
+    X *thrv_x = reinterpret_cast<X *>(base + CL.main + CL.vec);
     __shared__ double red[32];
     __shared__ XC piv3[3];
-    X *dinv = cv.take<X>(ld);
-    X *thrv_x = cv.take<X>(ld);
-    // the XC stage lives in the same arrays (XC is no wider than X)
-    XC *Wc = reinterpret_cast<XC *>(W), *Rc = reinterpret_cast<XC *>(R);
-    XC *Mwc = reinterpret_cast<XC *>(Mw), *Mc = reinterpret_cast<XC *>(M);
     XC *dinvc = reinterpret_cast<XC *>(dinv), *thrv = reinterpret_cast<XC *>(thrv_x);
     const int tid = threadIdx.x, bd = blockDim.x;
     const double *P2 = a.PG;
     const double *G = a.PG + (int64_t)a.rmax * a.cmax;
 
     // Ptot over all (l, j) at once (the global loads spread over the CTA),
-    // then the squared column norms of the block from the squares in Mw
-    // (Mw holds ld^2 8-byte entries; with r g beyond that, per column)
-    double *sq = reinterpret_cast<double *>(Mw);
+    // then the squared column norms of the block from the squares kept at
+    // the base of the work area (ld^2 8-byte entries; with r g beyond that,
+    // per column)
+    double *sq = reinterpret_cast<double *>(base);
     const bool spread = r * g <= ld * ld;
     if (spread)
         for (int e = tid; e < r * g; e += bd) {
@@ -788,7 +836,8 @@ __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
     }
     tri_inv<XC>(Rc, ld, g, Mwc, ld, Mc, ld, dinvc);
     // round M1 to the storage type: that is the matrix the QR2 pass applies;
-    // its X copy goes to R's array (the XC factor is no longer needed)
+    // its X copy goes to R's array (over Wc and Rc, no longer needed; R ends
+    // before Mc starts)
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
         const double v = round_to(a.dtype, XOps<XC>::to(Mc[i * ld + j]));
@@ -796,18 +845,24 @@ __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
         R[i * ld + j] = XOps<X>::from(v);
     }
     __syncthreads();
-    tri_inv<X>(R, ld, g, Mw, ld, W, ld, dinv);
-    for (int e = tid; e < g * g; e += bd) {
-        const int i = e / g, j = e % g;
-        a.R1p[i * ld + j] = XOps<X>::to(W[i * ld + j]);
-    }
+    tri_inv_out<X>(R, ld, g, Mw, ld, a.R1p, ld, dinv);
 }
 
-size_t small_chol_smem(int cmax) { return 4 * al16x((size_t)cmax * cmax * 8) + 2 * al16x((size_t)cmax * 8) + 64; }
+size_t small_chol_smem(int cmax, int dtype, int cond) {
+    const int xs = 8, xcs = (dtype == POD_F32 && !cond) ? 4 : 8;
+    return chol1_layout(cmax, xs, xcs).total;
+}
 
-pod_status launch_small_chol(const SmallArgs &a, cudaStream_t s) {
-    const size_t smem = a.gws_chol ? 64 : small_chol_smem(a.cmax);
-    if (smem > 220 * 1024) return POD_EUNSUPPORTED;
+pod_status launch_small_chol(const SmallArgs &a0, cudaStream_t s) {
+    // shared memory when this form's layout fits, else the global scratch
+    SmallArgs a = a0;
+    size_t smem = small_chol_smem(a.cmax, a.dtype, a.cond);
+    if (smem <= 220 * 1024) {
+        a.gws_chol = nullptr;
+    } else {
+        if (!a.gws_chol) return POD_EUNSUPPORTED;
+        smem = 64;
+    }
     const int nthr = a.cmax > 64 ? CHOL1_MAX_THREADS : 512;
     if (a.dtype == POD_F32 && !a.cond) {
         POD_CUDA_TRY(cudaFuncSetAttribute(k_small_chol<dfloat, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
