@@ -302,8 +302,10 @@ def kernel_model(m, es, r, g):
     (what the method must move)."""
     return {
         "proj": (m * (r + g) * es, 2.0 * m * r * g),
-        "cgs_gram": (m * (r + g) * es, 4.0 * m * r * g + 1.0 * m * g * g),
-        "qr2_gram": (m * (r + g) * es + m * g * es, 4.0 * m * r * g + 2.0 * m * g * g),
+        # CGS: read U, C; write Z = C - U P.  Z = C - U P, P2 = U^T Z, Z^T Z
+        "cgs_gram": (m * (r + g) * es + m * g * es, 4.0 * m * r * g + 1.0 * m * g * g),
+        # QR2: read U, Z; write W over Z.  Z - U P2, W = (.) M1 (triangular), W^T W
+        "qr2_gram": (m * (r + g) * es + m * g * es, 2.0 * m * r * g + 2.0 * m * g * g),
         "update": (m * (r + g) * es + m * r * es, 2.0 * m * (r + g) * r),
     }
 
