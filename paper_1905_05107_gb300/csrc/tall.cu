@@ -317,11 +317,19 @@ __device__ void gram_acc_comp(const T *X, int na, int ld, int bm, double *acc) {
     __syncthreads();
 }
 
+// Offset of row k of an upper-triangular matrix stored with its rows trimmed
+// to whole 4-column chunks: row k holds columns 4 floor(k / 4) .. n4 - 1.
+__host__ __device__ inline size_t tri_row_off(int k, int n4) {
+    const int a = k >> 2, b = k & 3;
+    return (size_t)4 * a * n4 - (size_t)8 * a * (a - 1) + (size_t)b * (n4 - 4 * a);
+}
+
 // Row-space products on a slab, tiled 4 rows x 4 output columns:
 // a1 = A1 S1 (K1 terms), a2 = A2 S2 (K2 terms); A1, A2 column-major (ld);
 // S1, S2 row-major with leading dimensions ls1, ls2; tri: S1 is upper
-// triangular (terms k > column skipped).  store(rc, cj, a1, a2) consumes
-// the tile of row chunk rc and column chunk cj.
+// triangular with trimmed rows (tri_row_off with n4 = ls1; terms k > column
+// skipped).  store(rc, cj, a1, a2) consumes the tile of row chunk rc and
+// column chunk cj.
 template <typename T, typename Store>
 __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K1, const T *S1, int ls1,
                                                const T *A2, int K2, const T *S2, int ls2, int ld, bool tri,
@@ -335,10 +343,13 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
 #pragma unroll
             for (int v = 0; v < 4; ++v) a1[u][v] = a2[u][v] = (T)0;
         const int k1end = tri ? min(K1, 4 * cj + 4) : K1;
+        size_t soff = 4 * cj;   // S1 offset of (k, 4 cj)
         for (int k = 0; k < k1end; ++k) {
             T x[4], s[4];
             lds4(A1 + (size_t)k * ld + ((rc ^ ((k >> 2) & msk)) << 2), x);
-            lds4(S1 + (size_t)k * ls1 + 4 * cj, s);
+            lds4(S1 + soff, s);
+            // trimmed rows: row k is ls1 - 4 floor(k / 4) long and starts at column 4 floor(k / 4)
+            soff += tri ? (size_t)(ls1 - 4 * (k >> 2) - ((k & 3) == 3 ? 4 : 0)) : (size_t)ls1;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -369,7 +380,7 @@ struct SmemPlan {
 // Shared-memory layout of one pass: only what that kind uses.
 //   PROJ    acc1 = P (r4 x c4)
 //   CGS     S1 = P (r4 x c4); acc1 = P2 (r4 x c4); acc2 = Z^T Z (upper tiles)
-//   QR2     W slab; S2 = P2 (r4 x c4), S3 = M1 (c4 x c4); acc2 = W^T W (upper tiles)
+//   QR2     W slab; S2 = P2 (r4 x c4), S3 = M1 (trimmed rows); acc2 = W^T W (upper tiles)
 //   UPDATE  S1 = X (r4 x r4), S2 = Y (c4 x r4)
 __host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm, int kind) {
     SmemPlan p;
@@ -381,7 +392,7 @@ __host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm, int ki
     p.ws = kind == TALL_QR2 ? (size_t)p.c4 * p.ld : 0;
     p.s1 = kind == TALL_CGS ? (size_t)p.r4 * p.c4 : (kind == TALL_UPDATE ? (size_t)p.r4 * p.r4 : 0);
     p.s2 = kind == TALL_QR2 || kind == TALL_UPDATE ? (size_t)p.c4 * p.r4 : 0;
-    p.s3 = kind == TALL_QR2 ? (size_t)p.c4 * p.c4 : 0;
+    p.s3 = kind == TALL_QR2 ? tri_row_off(p.c4, p.c4) : 0;   // M1, trimmed rows
     p.acc1 = kind == TALL_PROJ || kind == TALL_CGS ? (size_t)p.r4 * p.c4 : 0;
     p.acc2 = kind == TALL_CGS || kind == TALL_QR2 ? tri : 0;
     return p;
@@ -571,9 +582,11 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         }
     }
     if (KIND == TALL_QR2) {
+        // M1 with trimmed rows (tri_row_off, n4 = g4)
         for (int e = tid; e < g4 * g4; e += bd) {
             const int l = e / g4, j = e - l * g4;
-            S3[e] = (l < g && j < g && l <= j) ? (T)a.M1[l * a.cmax + j] : (T)0;
+            if (j < 4 * (l >> 2)) continue;
+            S3[tri_row_off(l, g4) + j - 4 * (l >> 2)] = (l < g && j < g && l <= j) ? (T)a.M1[l * a.cmax + j] : (T)0;
         }
         for (int e = tid; e < (g4 - g) * ld; e += bd) Ws[(size_t)g * ld + e] = (T)0;
     }
@@ -911,7 +924,7 @@ TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
     };
     // two resident CTAs per SM (16 warps) when every kind fits in 110 KB with
     // slabs of at least 32 rows; else one CTA per SM, each kind with the
-    // tallest slab whose layout fits in 200 KB; a kind that does not fit even
+    // tallest slab whose layout fits in 220 KB; a kind that does not fit even
     // with 16-row slabs keeps its coefficient tiles and accumulators in global
     // scratch (wide)
     int per_sm = 2;
@@ -927,7 +940,7 @@ TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
         for (int k = 0; k < 4; ++k) {
             int bm = 0;
             for (int b = 128; b >= 16 && !bm; b >>= 1)
-                if (bytes_for(b, k) <= 200 * 1024) bm = b;
+                if (bytes_for(b, k) <= 220 * 1024) bm = b;
             p.wide_k[k] = 0;
             if (bm) {
                 p.bm_k[k] = bm;
