@@ -108,7 +108,8 @@ struct TallPlan {
     int64_t gstride;        // bytes of scratch per CTA (wide kinds)
     int bm_k[4];            // per TallKind: slab rows,
     size_t smem_k[4];       //   dynamic shared memory,
-    int wide_k[4];          //   whether it uses the global scratch
+    int wide_k[4];          //   whether it uses the global scratch,
+    int threads_k[4];       //   threads per CTA
 };
 
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms);

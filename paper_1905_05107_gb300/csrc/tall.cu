@@ -28,7 +28,8 @@
 
 namespace {
 
-constexpr int TALL_THREADS = 256;
+constexpr int TALL_THREADS = 256;       // k_atu; k_tall when two CTAs share an SM
+constexpr int TALL_MAX_THREADS = 512;   // k_tall with one CTA per SM (tall_plan picks)
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
@@ -399,16 +400,16 @@ __host__ __device__ inline SmemPlan smem_plan(int rmax, int cmax, int bm, int ki
 }
 
 template <typename T>
-__host__ __device__ inline size_t smem_bytes(const SmemPlan &p) {
+__host__ __device__ inline size_t smem_bytes(const SmemPlan &p, int threads) {
     return (2 * p.buf + p.ws + p.s1 + p.s2 + p.s3) * sizeof(T) + (p.acc1 + p.acc2) * 8 +
-           (size_t)TALL_THREADS * 16 * sizeof(T) + 64;
+           (size_t)threads * 16 * sizeof(T) + 64;
 }
 // Wide plans keep only the slab buffers and the reduction tile in shared
 // memory; the coefficient tiles S1..S3 and the FP64 accumulators live in the
 // CTA's slice of global scratch (L2-resident).
 template <typename T>
-__host__ __device__ inline size_t smem_bytes_wide(const SmemPlan &p) {
-    return (2 * p.buf + p.ws) * sizeof(T) + (size_t)TALL_THREADS * 16 * sizeof(T) + 64;
+__host__ __device__ inline size_t smem_bytes_wide(const SmemPlan &p, int threads) {
+    return (2 * p.buf + p.ws) * sizeof(T) + (size_t)threads * 16 * sizeof(T) + 64;
 }
 template <typename T>
 __host__ __device__ inline size_t gscratch_bytes(const SmemPlan &p) {
@@ -418,7 +419,7 @@ __host__ __device__ inline size_t gscratch_bytes(const SmemPlan &p) {
 // The second CholeskyQR Gram must be near I on its kept indices; if not, the
 // first pass lost accuracy (an ill-conditioned residual block): flag the
 // round for the compensated rerun (or'ed with the first Cholesky's drop
-// test).  Run by one whole CTA of TALL_THREADS threads on the final G2.
+// test).  Run by one whole CTA on the final G2.
 __device__ void g2_check(const double *G2, int g, int cmax, DevState *st) {
     const int tid = threadIdx.x, bd = blockDim.x;
     double dev = 0.0;
@@ -434,7 +435,7 @@ __device__ void g2_check(const double *G2, int g, int cmax, DevState *st) {
         const double y = __shfl_xor_sync(0xffffffffu, dev, o);
         dev = y > dev ? y : dev;
     }
-    __shared__ double wmax[TALL_THREADS / 32];
+    __shared__ double wmax[TALL_MAX_THREADS / 32];
     if ((tid & 31) == 0) wmax[tid >> 5] = dev;
     __syncthreads();
     if (tid == 0) {
@@ -529,7 +530,7 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sum_parts(SumParts a) {
 }
 
 template <typename T, int KIND>
-__global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
+__global__ void __launch_bounds__(TALL_MAX_THREADS) k_tall(TallArgs<T> a) {
     const DevState *st = a.st;
     if (st->done) return;
     if (a.cond && !st->robust) return;
@@ -559,7 +560,7 @@ __global__ void __launch_bounds__(TALL_THREADS) k_tall(TallArgs<T> a) {
         acc2 = acc1 + L.acc1;
         red = reinterpret_cast<T *>(acc2 + L.acc2);
     }
-    int *s_flag = reinterpret_cast<int *>(red + TALL_THREADS * 16);
+    int *s_flag = reinterpret_cast<int *>(red + blockDim.x * 16);
     const int tid = threadIdx.x, bd = blockDim.x;
     const int r4 = round4(r), g4 = round4(g), rn4 = round4(rn);
     const bool vec = a.vec != 0;
@@ -895,7 +896,8 @@ pod_status launch_kind(const TallArgs<T> &a0, const TallPlan &plan, cudaStream_t
     if (!plan.wide_k[KIND]) a.gscratch = nullptr;
     const size_t smem = plan.smem_k[KIND];
     POD_CUDA_TRY(cudaFuncSetAttribute(k_tall<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tall<T, KIND><<<plan.grid, TALL_THREADS, smem, st>>>(a);
+    const int threads = plan.threads_k[KIND] ? plan.threads_k[KIND] : TALL_THREADS;
+    k_tall<T, KIND><<<plan.grid, threads, smem, st>>>(a);
     POD_CUDA_TRY(cudaGetLastError());
     return POD_OK;
 }
@@ -911,40 +913,66 @@ pod_status launch_sum_parts(const SumParts &a, int cols_cap, cudaStream_t s) {
 }
 
 
+// Threads of a one-CTA-per-SM pass: enough that each of its tile loops
+// (row-space tiles of a slab, Gram tiles) takes one round, within 256..512.
+static int tall_threads_for(int kind, int bm, int rmax, int cmax) {
+    const int rt = round4(rmax) / 4, ct = round4(cmax) / 4, ch = bm / 4;
+    int tiles = 0;
+    auto mx = [&](int t) { tiles = t > tiles ? t : tiles; };
+    if (kind == TALL_PROJ) mx(rt * ct);
+    if (kind == TALL_CGS) {
+        mx(ch * ct);
+        mx(rt * ct);
+        mx(ct * (ct + 1) / 2);
+    }
+    if (kind == TALL_QR2) {
+        mx(ch * ct);
+        mx(ct * (ct + 1) / 2);
+    }
+    if (kind == TALL_UPDATE) mx(ch * rt);
+    int th = (tiles + 31) / 32 * 32;
+    return th < TALL_THREADS ? TALL_THREADS : (th > TALL_MAX_THREADS ? TALL_MAX_THREADS : th);
+}
+
 TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
     TallPlan p{};
     const bool f32 = dtype == POD_F32;
-    auto bytes_for = [&](int bm, int kind) {
+    auto bytes_for = [&](int bm, int kind, int th) {
         SmemPlan L = smem_plan(rmax, cmax, bm, kind);
-        return f32 ? smem_bytes<float>(L) : smem_bytes<double>(L);
+        return f32 ? smem_bytes<float>(L, th) : smem_bytes<double>(L, th);
     };
     auto wide_for = [&](int bm, int kind) {
         SmemPlan L = smem_plan(rmax, cmax, bm, kind);
-        return f32 ? smem_bytes_wide<float>(L) : smem_bytes_wide<double>(L);
+        return f32 ? smem_bytes_wide<float>(L, TALL_THREADS) : smem_bytes_wide<double>(L, TALL_THREADS);
     };
     // two resident CTAs per SM (16 warps) when every kind fits in 110 KB with
-    // slabs of at least 32 rows; else one CTA per SM, each kind with the
-    // tallest slab whose layout fits in 220 KB; a kind that does not fit even
-    // with 16-row slabs keeps its coefficient tiles and accumulators in global
-    // scratch (wide)
+    // slabs of at least 32 rows and 256 threads; else one CTA per SM, each
+    // kind with the tallest slab whose layout fits in 220 KB and as many
+    // threads as its tile loops can use (tall_threads_for); a kind that does
+    // not fit even with 16-row slabs keeps its coefficient tiles and
+    // accumulators in global scratch (wide, 256 threads)
     int per_sm = 2;
     for (int k = 0; k < 4 && per_sm == 2; ++k) {
         int bm = 0;
         for (int b = 128; b >= 32 && !bm; b >>= 1)
-            if (bytes_for(b, k) <= 110 * 1024) bm = b;
+            if (bytes_for(b, k, TALL_THREADS) <= 110 * 1024) bm = b;
         if (!bm) per_sm = 1;
         p.bm_k[k] = bm;
-        p.smem_k[k] = bm ? bytes_for(bm, k) : 0;
+        p.smem_k[k] = bm ? bytes_for(bm, k, TALL_THREADS) : 0;
+        p.threads_k[k] = TALL_THREADS;
     }
     if (per_sm == 1) {
         for (int k = 0; k < 4; ++k) {
-            int bm = 0;
-            for (int b = 128; b >= 16 && !bm; b >>= 1)
-                if (bytes_for(b, k) <= 220 * 1024) bm = b;
+            int bm = 0, th = TALL_THREADS;
+            for (int b = 128; b >= 16 && !bm; b >>= 1) {
+                th = tall_threads_for(k, b, rmax, cmax);
+                if (bytes_for(b, k, th) <= 220 * 1024) bm = b;
+            }
             p.wide_k[k] = 0;
             if (bm) {
                 p.bm_k[k] = bm;
-                p.smem_k[k] = bytes_for(bm, k);
+                p.smem_k[k] = bytes_for(bm, k, th);
+                p.threads_k[k] = th;
                 continue;
             }
             bm = 16;
@@ -956,6 +984,7 @@ TallPlan tall_plan(int dtype, int64_t m, int rmax, int cmax, int num_sms) {
             SmemPlan L = smem_plan(rmax, cmax, bm, k);
             p.bm_k[k] = bm;
             p.smem_k[k] = wide_for(bm, k);
+            p.threads_k[k] = TALL_THREADS;
             p.wide_k[k] = 1;
             const int64_t gs = (int64_t)(f32 ? gscratch_bytes<float>(L) : gscratch_bytes<double>(L));
             if (gs > p.gstride) p.gstride = gs;
