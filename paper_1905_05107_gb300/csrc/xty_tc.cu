@@ -27,8 +27,8 @@
 // CTA roles (512 threads):
 //   warp 0      producer: TMA copies of each slab into a ring, 128-byte
 //               swizzled (the layout the MMA descriptors read): X as one box
-//               of 128 columns (dense) or one 32-row box per sampled column
-//               (gathered; lanes issue them in parallel), Y as one box; also
+//               of 128 columns (dense) or four sampled columns per
+//               tile::gather4 copy (gathered; one copy per lane), Y as one box; also
 //               allocates / frees TMEM
 //   warp 1      one thread issues the MMAs (M = 128, N = NT) into one of two
 //               TMEM accumulators, commits free a stage and, at the end of a
@@ -87,22 +87,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
     return false;
 }
 
-// 16-byte asynchronous copy global -> shared; src_bytes < 16 zero-fills the rest.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa(smem)), "l"(gmem), "r"(src_bytes)
-                 : "memory");
-}
-// Arrive on the barrier once this thread's earlier cp.async copies have landed
-// (the barrier's expected count includes these arrivals).
-__device__ __forceinline__ void cp_async_arrive(uint64_t *b) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(sa(b)) : "memory");
-}
-
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::
             "r"(sa(dst)),
         "l"(map), "r"(sa(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Four columns c0..c3 of a 2-D tensor map with a box of 32 rows x 1 column
+// (tile::gather4): 4 x 128 bytes into four consecutive 128-byte rows at dst,
+// swizzled as the map says; rows x .. x + 31 (x a multiple of 32).
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];\n" ::"r"(sa(dst)),
+        "l"(map), "r"(sa(bar)), "r"(x), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
 
@@ -249,9 +250,8 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
 
     if (tid == 0) {
         for (int s = 0; s < L::RS; ++s) {
-            // the producer's expect_tx arrival, plus one cp.async arrival per
-            // lane when the X columns are gathered
-            mbar_init(&full[s], a.gather ? 33 : 1);
+            // the producer's expect_tx arrival (the copies complete by bytes)
+            mbar_init(&full[s], 1);
             mbar_init(&rfree[s], L::INPLACE ? 1 : 128);
         }
         for (int s = 0; s < L::CS; ++s) {
@@ -286,8 +286,8 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
-        int col[4];   // gathered: this lane's columns of the current M-tile
-        int cur_mt = -1, ncol_mt = 0;
+        int gcol[4];   // gathered: the columns of this lane's group of four (M-tile rows 4 lane ..)
+        int cur_mt = -1, ncol_mt = 0, ngrp = 0;
         for (int kc = 0; kc < nit; ++kc) {
             const int s = kc % L::RS;
             // lane 0 decides, the warp follows (every lane reaches the shuffle)
@@ -304,14 +304,17 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                 cur_mt = mt;
                 const int64_t c0 = (int64_t)mt * XT_TM;
                 ncol_mt = ncols - c0 < XT_TM ? (int)(ncols - c0) : XT_TM;
+                ngrp = (ncol_mt + 3) / 4;
+                // rows past the last column repeat the group's first column
+                // (their products are never read)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int j = lane + 32 * q;
-                    col[q] = j < ncol_mt ? a.idx[c0 + j] : 0;
+                    const int j = 4 * lane + q;
+                    gcol[q] = lane < ngrp ? a.idx[c0 + (j < ncol_mt ? j : 4 * lane)] : 0;
                 }
             }
             unsigned char *stg = raw_stage(s);
-            const uint32_t xbytes = a.gather ? 0u : (uint32_t)L::XB32 * L::BOXES;
+            const uint32_t xbytes = a.gather ? (uint32_t)ngrp * 512u * L::BOXES : (uint32_t)L::XB32 * L::BOXES;
             if (lane == 0) mbar_expect_tx(&full[s], xbytes + (uint32_t)L::YB32 * L::BOXES);
             __syncwarp();
 #pragma unroll
@@ -319,29 +322,16 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                 unsigned char *xdst = stg + (L::INPLACE ? 0 : bx * L::XB32);
                 unsigned char *ydst = stg + (L::INPLACE ? 2 * L::XB32 : L::BOXES * L::XB32 + bx * L::YB32);
                 if (a.gather) {
-                    // sampled column j: its 32 rows (128 bytes) as 8 16-byte
-                    // copies into row j of the tile, chunk c at the 128-byte
-                    // swizzled position (c ^ (j & 7)); rows beyond m read as 0
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = lane + 32 * q;
-                        if (j < ncol_mt) {
-                            const float *src = a.X + (int64_t)col[q] * a.ldx;
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                const int64_t rr = (int64_t)x + 32 * bx + 4 * c;
-                                const int bytes = rr < a.m ? 16 : 0;
-                                cp_async16(xdst + j * 128 + ((c ^ (j & 7)) << 4), src + (bytes ? rr : 0), bytes);
-                            }
-                        }
-                    }
+                    // sampled columns 4 lane .. 4 lane + 3: their 32 rows
+                    // (128 bytes each) into tile rows 4 lane .. by one TMA
+                    // gather (128-byte swizzle; rows beyond m read as 0)
+                    if (lane < ngrp)
+                        tma_gather4(xdst + lane * 512, &mapX, &full[s], x + 32 * bx, gcol[0], gcol[1], gcol[2], gcol[3]);
                 } else if (lane == 0) {
                     tma_2d(xdst, &mapX, &full[s], x + 32 * bx, mt * XT_TM);
                 }
                 if (lane == 0) tma_2d(ydst, &mapY, &full[s], x + 32 * bx, 0);
             }
-            // each lane's copies arrive on the stage's barrier when they land
-            if (a.gather) cp_async_arrive(&full[s]);
             if (lane == 0) s_issued = kc + 1;
             __syncwarp();
         }
@@ -664,11 +654,9 @@ pod_status launch_xty_tc(const XtyTcArgs &a0, const XtyTcPlan &plan, const float
     CUtensorMap mX, mY;
     a.X = X;
     a.ldx = ldx;
-    // dense X: boxes of 128 columns; gathered X is copied with cp.async (the
-    // map is then unused)
+    // dense X: boxes of 128 columns; gathered X: one-column boxes (tile::gather4)
     if (!make_map(&mY, Y, a.m, ycols, a.m, plan.nt)) return POD_EUNSUPPORTED;
-    if (a.gather) mX = mY;
-    else if (!make_map(&mX, X, a.m, xcols, ldx, XT_TM)) return POD_EUNSUPPORTED;
+    if (!make_map(&mX, X, a.m, xcols, ldx, a.gather ? 1 : XT_TM)) return POD_EUNSUPPORTED;
     const int mode = plan.mode;
     if (plan.nt == 32) {
         if (mode == POD_PREC_TF32X3) return launch_one<POD_PREC_TF32X3, 32>(mX, mY, a, plan, s);
