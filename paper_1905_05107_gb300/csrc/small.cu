@@ -114,36 +114,6 @@ __device__ void tri_inv(const X *R, int ldr, int n, X *Mw, int ldw, X *M, int ld
     }
 }
 
-// As tri_inv, with M = R^{-1} written straight to the FP64 array out (ld
-// ldo; the whole n x n block, zeros below the diagonal and in the rows and
-// columns of dropped indices).
-template <typename X>
-__device__ void tri_inv_out(const X *R, int ldr, int n, X *Mw, int ldw, double *out, int ldo, X *dinv) {
-    const int tid = threadIdx.x, bd = blockDim.x;
-    for (int e = tid; e < n * n; e += bd) {
-        const int i = e / n, j = e % n;
-        Mw[i * ldw + j] = (i == j) ? XOps<X>::one() : XOps<X>::zero();
-        out[i * ldo + j] = 0.0;
-    }
-    for (int k = tid; k < n; k += bd) {
-        const X d = R[k * ldr + k];
-        dinv[k] = x_hi(d) != 0.f ? XOps<X>::one() / d : XOps<X>::zero();
-    }
-    const int NC = col_lanes(n, bd), RS = bd / NC;
-    const int jt = tid & (NC - 1), it = tid / NC;
-    __syncthreads();
-    for (int k = n - 1; k >= 0; --k) {
-        const X inv = dinv[k];
-        if (x_hi(inv) != 0.f && it < RS)
-            for (int j = k + jt; j < n; j += NC) {
-                const X mkj = Mw[k * ldw + j] * inv;
-                if (it == 0) out[k * ldo + j] = XOps<X>::to(mkj);
-                for (int i = it; i < k; i += RS) Mw[i * ldw + j] = Mw[i * ldw + j] - R[i * ldr + k] * mkj;
-            }
-        __syncthreads();
-    }
-}
-
 // C = A B for upper triangular A, B (all entries in parallel).
 template <typename X>
 __device__ void trmm_upper(const X *A, int lda, const X *B, int ldb, int n, X *C, int ldc) {
@@ -727,9 +697,115 @@ pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t
 // before use, so an FP32 inverse costs no accuracy: both errors are
 // O(u kappa)); X (double-float or FP64) in the compensated rerun and for FP64
 // data.  R1p, the inverse of the applied M1, is always formed in X.
+// ---------------------------------------------------------------------------
+// Blocked forms of chol_drop and tri_inv for the first CholeskyQR kernel
+// (CB-row blocks: a few barriers per block instead of one per row).
+// ---------------------------------------------------------------------------
+constexpr int CB = 8;
+
+// Right-looking Cholesky with the pivot drops of chol_drop (a pivot not
+// above its floor (thrv[k], else thr) gives a zero row of R).  W: upper
+// triangle (ld ldw), updated in place; R: upper triangular factor (ld ldr).
+// Warp 0 forms each CB-row panel of R (row k: W[k][j] minus the panel rows
+// above it, divided by the pivot), then all threads subtract the panel's
+// rank-CB product from the trailing upper triangle of W.
+template <typename X>
+__device__ void chol_drop_blk(X *W, int ldw, int n, X thr, X *R, int ldr, const X *thrv) {
+    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31;
+    for (int e = tid; e < n * n; e += bd) {
+        const int i = e / n, j = e - i * n;
+        if (i > j) R[i * ldr + j] = XOps<X>::zero();
+    }
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += CB) {
+        const int k1 = k0 + CB < n ? k0 + CB : n;
+        if (tid < 32) {
+            for (int k = k0; k < k1; ++k) {
+                X d = W[k * ldw + k];
+                for (int l = k0; l < k; ++l) d = d - R[l * ldr + k] * R[l * ldr + k];
+                const bool keep = x_gt(d, thrv ? thrv[k] : thr);
+                X p = XOps<X>::zero(), inv_p = XOps<X>::zero();
+                if (keep) {
+                    p = XOps<X>::sqrt_(d);
+                    inv_p = XOps<X>::one() / p;
+                }
+                for (int j = k + lane; j < n; j += 32) {
+                    X w = W[k * ldw + j];
+                    for (int l = k0; l < k; ++l) w = w - R[l * ldr + k] * R[l * ldr + j];
+                    R[k * ldr + j] = keep ? (j == k ? p : w * inv_p) : XOps<X>::zero();
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        const int nt = n - k1;
+        for (int e = tid; e < nt * nt; e += bd) {
+            const int i = k1 + e / nt, j = k1 + e % nt;
+            if (i > j) continue;
+            X w = W[i * ldw + j];
+            for (int l = k0; l < k1; ++l) w = w - R[l * ldr + i] * R[l * ldr + j];
+            W[i * ldw + j] = w;
+        }
+        __syncthreads();
+    }
+}
+
+// M = R^{-1} for upper triangular R (zero pivots of dropped indices give
+// zero rows and columns of M): the CB x CB diagonal blocks by back
+// substitution (a thread per column), then the blocks at block distance
+// 1, 2, ...: M_IJ = -M_II (sum_{K = I+1..J} R_IK M_KJ).  T: scratch of
+// ceil(n / CB) CB^2 entries.
+template <typename X>
+__device__ void tri_inv_blk(const X *R, int ldr, int n, X *M, int ldm, X *T, X *dinv) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int nb = (n + CB - 1) / CB;
+    for (int e = tid; e < n * n; e += bd) {
+        const int i = e / n, j = e - i * n;
+        M[i * ldm + j] = XOps<X>::zero();
+    }
+    for (int k = tid; k < n; k += bd) {
+        const X d = R[k * ldr + k];
+        dinv[k] = x_hi(d) != 0.f ? XOps<X>::one() / d : XOps<X>::zero();
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += bd) {
+        const int i0 = (j / CB) * CB;
+        M[j * ldm + j] = dinv[j];
+        for (int i = j - 1; i >= i0; --i) {
+            X sum = XOps<X>::zero();
+            for (int l = i + 1; l <= j; ++l) sum = sum + R[i * ldr + l] * M[l * ldm + j];
+            M[i * ldm + j] = XOps<X>::zero() - sum * dinv[i];
+        }
+    }
+    __syncthreads();
+    for (int dl = 1; dl < nb; ++dl) {
+        const int np = nb - dl;
+        for (int e = tid; e < np * CB * CB; e += bd) {
+            const int bi = e / (CB * CB), rem = e - bi * CB * CB;
+            const int i = bi * CB + rem / CB, j = (bi + dl) * CB + rem % CB;
+            X sum = XOps<X>::zero();
+            if (i < n && j < n)
+                for (int l = (bi + 1) * CB; l <= j; ++l) sum = sum + R[i * ldr + l] * M[l * ldm + j];
+            T[e] = sum;
+        }
+        __syncthreads();
+        for (int e = tid; e < np * CB * CB; e += bd) {
+            const int bi = e / (CB * CB), rem = e - bi * CB * CB, ii = rem / CB, jj = rem % CB;
+            const int i = bi * CB + ii, j = (bi + dl) * CB + jj;
+            if (i >= n || j >= n) continue;
+            const int iend = (bi + 1) * CB < n ? (bi + 1) * CB : n;
+            X sum = XOps<X>::zero();
+            for (int l = i; l < iend; ++l) sum = sum + M[i * ldm + l] * T[bi * CB * CB + (l - bi * CB) * CB + jj];
+            M[i * ldm + j] = XOps<X>::zero() - sum;
+        }
+        __syncthreads();
+    }
+}
+
 struct Chol1Layout {
     size_t xc, x;      // one ld x ld array of XC / of X (16-byte multiples)
-    size_t main;       // the larger of 4 xc and 2 x
+    size_t main;       // the larger of 3 xc and 2 x
+    size_t t;          // the blocked inverse's scratch (ceil(ld / CB) CB^2 X)
     size_t vec;        // one length-ld X vector
     size_t total;
 };
@@ -737,10 +813,11 @@ __host__ __device__ inline Chol1Layout chol1_layout(int ld, int xs, int xcs) {
     Chol1Layout L;
     L.xc = al16x((size_t)ld * ld * xcs);
     L.x = al16x((size_t)ld * ld * xs);
-    L.main = 4 * L.xc > 2 * L.x ? 4 * L.xc : 2 * L.x;
+    L.main = 3 * L.xc > 2 * L.x ? 3 * L.xc : 2 * L.x;
     if (L.main < L.x) L.main = L.x;   // the column-norm squares (ld^2 doubles)
+    L.t = al16x((size_t)((ld + CB - 1) / CB) * CB * CB * xs);
     L.vec = al16x((size_t)ld * xs);
-    L.total = L.main + 2 * L.vec + 64;
+    L.total = L.main + L.t + 2 * L.vec + 64;
     return L;
 }
 
@@ -752,18 +829,19 @@ __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
     const int r = st->r_cur, g = st->g, nc = r + g;
     const int ld = a.cmax;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // layout (chol1_layout): the XC stage's four ld x ld XC arrays, or the
-    // X stage's two ld x ld X arrays, over the same bytes; then dinv and the
-    // pivot floors
+    // layout (chol1_layout): the XC stage's three ld x ld XC arrays (W, R,
+    // M), or the X stage's two ld x ld X arrays (M1, its inverse), over the
+    // same bytes; then the blocked inverse's scratch, dinv and the pivot
+    // floors
     const Chol1Layout CL = chol1_layout(ld, (int)sizeof(X), (int)sizeof(XC));
     unsigned char *base = a.gws_chol ? a.gws_chol : smem_raw;
     XC *Wc = reinterpret_cast<XC *>(base), *Rc = reinterpret_cast<XC *>(base + CL.xc);
-    XC *Mwc = reinterpret_cast<XC *>(base + 2 * CL.xc), *Mc = reinterpret_cast<XC *>(base + 3 * CL.xc);
-    X *R = reinterpret_cast<X *>(base), *Mw = reinterpret_cast<X *>(base + CL.x);
-    X *dinv = reinterpret_cast<X *>(base + CL.main);
-    X *thrv_x = reinterpret_cast<X *>(base + CL.main + CL.vec);
+    XC *Mc = reinterpret_cast<XC *>(base + 2 * CL.xc);
+    X *R = reinterpret_cast<X *>(base), *Mx = reinterpret_cast<X *>(base + CL.x);
+    unsigned char *tb = base + CL.main;   // blocked-inverse scratch
+    X *dinv = reinterpret_cast<X *>(base + CL.main + CL.t);
+    X *thrv_x = reinterpret_cast<X *>(base + CL.main + CL.t + CL.vec);
     __shared__ double red[32];
-    __shared__ XC piv3[3];
     XC *dinvc = reinterpret_cast<XC *>(dinv), *thrv = reinterpret_cast<XC *>(thrv_x);
     const int tid = threadIdx.x, bd = blockDim.x;
     const double *P2 = a.PG;
@@ -821,7 +899,7 @@ __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
         Wc[i * ld + j] = XOps<XC>::from(i <= j ? G[i * ld + j] : 0.0);
     }
     __syncthreads();
-    chol_drop<XC>(Wc, ld, g, thr, Rc, ld, piv3, thrv);
+    chol_drop_blk<XC>(Wc, ld, g, thr, Rc, ld, thrv);
     if (!a.cond) {
         // a column the plain FP32 pass dropped under its noise floor
         // 8 u G_jj may hide more than 8 u sigma_1: the round then takes the
@@ -834,10 +912,10 @@ __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
         flag = __syncthreads_or(flag);
         if (tid == 0) st->robust = flag;
     }
-    tri_inv<XC>(Rc, ld, g, Mwc, ld, Mc, ld, dinvc);
+    tri_inv_blk<XC>(Rc, ld, g, Mc, ld, reinterpret_cast<XC *>(tb), dinvc);
     // round M1 to the storage type: that is the matrix the QR2 pass applies;
     // its X copy goes to R's array (over Wc and Rc, no longer needed; R ends
-    // before Mc starts)
+    // where Mc starts)
     for (int e = tid; e < g * g; e += bd) {
         const int i = e / g, j = e % g;
         const double v = round_to(a.dtype, XOps<XC>::to(Mc[i * ld + j]));
@@ -845,7 +923,11 @@ __global__ void __launch_bounds__(CHOL1_MAX_THREADS) k_small_chol(SmallArgs a) {
         R[i * ld + j] = XOps<X>::from(v);
     }
     __syncthreads();
-    tri_inv_out<X>(R, ld, g, Mw, ld, a.R1p, ld, dinv);
+    tri_inv_blk<X>(R, ld, g, Mx, ld, reinterpret_cast<X *>(tb), dinv);
+    for (int e = tid; e < g * g; e += bd) {
+        const int i = e / g, j = e % g;
+        a.R1p[i * ld + j] = XOps<X>::to(Mx[i * ld + j]);
+    }
 }
 
 size_t small_chol_smem(int cmax, int dtype, int cond) {
