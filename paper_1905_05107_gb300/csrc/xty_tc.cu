@@ -33,7 +33,7 @@
 //   warp 1      one thread issues the MMAs (M = 128, N = NT) into one of two
 //               TMEM accumulators, commits free a stage and, at the end of a
 //               64-row group, hand the accumulator to the epilogue
-//   warps 4-7   split (TF32: in place, hi and a lo copy) or convert (BF16:
+//   warps 4-7   split (TF32: hi and lo tiles) or convert (BF16:
 //               from the raw FP32 ring into a bf16 ring) each landed slab
 //   warps 8-15  drain each group's accumulator into double-float registers
 //               (two warps per TMEM lane quadrant, half of the columns each,
@@ -173,13 +173,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 __device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
 
-// Ring layout of one (MODE, NT).  TF32: one ring, each stage holds the FP32
-// slab (split in place into hi) and its lo copy.  BF16: a raw FP32 ring the
-// copies land in and a bf16 ring the converter fills (b0, and b1 for X3).
+// Ring layout of one (MODE, NT): a raw FP32 ring the copies land in and a
+// ring of operand tiles the converter fills (TF32 hi and lo; bf16 b0, and b1
+// for X3).  A raw stage is free again once converted, before its MMAs run.
 template <int MODE, int NT>
 struct XtLayout {
-    static constexpr bool INPLACE = MODE == POD_PREC_TF32X3;
-    static constexpr int KROWS = INPLACE ? 32 : 64;          // rows per slab (128 bytes of K)
+    static constexpr int KROWS = MODE == POD_PREC_TF32X3 ? 32 : 64;   // rows per slab (128 bytes of K)
     static constexpr int BOXES = KROWS / 32;                  // 32-row FP32 boxes per slab
     static constexpr int PRODUCTS = MODE == POD_PREC_BF16 ? 1 : 3;
     static constexpr int GROUP = 64 / KROWS;                  // slabs per TMEM accumulation group
@@ -190,19 +189,17 @@ struct XtLayout {
     static constexpr int CX = XT_TM * 128, CY = NT * 128;     // one converted operand tile
     static constexpr int NCONV = PRODUCTS == 1 ? 1 : 2;       // tiles per operand
     static constexpr int CONV = NCONV * (CX + CY);
-    static constexpr int STAGE_INPLACE = 2 * (XB32 + YB32);
-    static constexpr int RS = INPLACE ? (XT_SMEM_BUDGET / STAGE_INPLACE > 4 ? 4 : XT_SMEM_BUDGET / STAGE_INPLACE)
-                                      : (3 * RAW + 2 * CONV <= XT_SMEM_BUDGET ? 3 : 2);
-    static constexpr int CS = INPLACE ? RS : (2 * RAW + 2 * CONV <= XT_SMEM_BUDGET ? 2 : 1);
-    static constexpr int RAW_BYTES = INPLACE ? RS * STAGE_INPLACE : RS * RAW;
-    static constexpr int CONV_BYTES = INPLACE ? 0 : CS * CONV;
+    static constexpr int CS = 2 * RAW + 2 * CONV <= XT_SMEM_BUDGET ? 2 : 1;
+    static constexpr int RS = 4 * RAW + CS * CONV <= XT_SMEM_BUDGET ? 4 : (3 * RAW + CS * CONV <= XT_SMEM_BUDGET ? 3 : 2);
+    static constexpr int RAW_BYTES = RS * RAW;
+    static constexpr int CONV_BYTES = CS * CONV;
     static constexpr int TMEM_COLS = 2 * NT <= 32 ? 32 : (2 * NT <= 64 ? 64 : (2 * NT <= 128 ? 128 : 256));
     static constexpr size_t SMEM = 1024 + (size_t)RAW_BYTES + CONV_BYTES + 256;
     // offsets inside a stage / conversion tile
     static constexpr int X_HI = 0;
-    static constexpr int X_LO = INPLACE ? XB32 : CX;
-    static constexpr int Y_HI = INPLACE ? 2 * XB32 : NCONV * CX;
-    static constexpr int Y_LO = INPLACE ? 2 * XB32 + YB32 : NCONV * CX + CY;
+    static constexpr int X_LO = CX;
+    static constexpr int Y_HI = NCONV * CX;
+    static constexpr int Y_LO = NCONV * CX + CY;
 };
 
 // Owner CTA of work item i when W items are cut into G equal contiguous ranges
@@ -252,7 +249,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         for (int s = 0; s < L::RS; ++s) {
             // the producer's expect_tx arrival (the copies complete by bytes)
             mbar_init(&full[s], 1);
-            mbar_init(&rfree[s], L::INPLACE ? 1 : 128);
+            mbar_init(&rfree[s], 128);   // the converter's threads
         }
         for (int s = 0; s < L::CS; ++s) {
             mbar_init(&ready[s], 128);
@@ -279,10 +276,10 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     const uint32_t tmem = s_tmem;
 
     auto raw_stage = [&](int s) {
-        return rawb + (size_t)s * (L::INPLACE ? L::STAGE_INPLACE : L::RAW);
+        return rawb + (size_t)s * L::RAW;
     };
     // operand tiles the MMA reads for slab stage cs
-    auto op_stage = [&](int cs) { return L::INPLACE ? raw_stage(cs) : convb + (size_t)cs * L::CONV; };
+    auto op_stage = [&](int cs) { return convb + (size_t)cs * L::CONV; };
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -319,8 +316,8 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             __syncwarp();
 #pragma unroll
             for (int bx = 0; bx < L::BOXES; ++bx) {
-                unsigned char *xdst = stg + (L::INPLACE ? 0 : bx * L::XB32);
-                unsigned char *ydst = stg + (L::INPLACE ? 2 * L::XB32 : L::BOXES * L::XB32 + bx * L::YB32);
+                unsigned char *xdst = stg + bx * L::XB32;
+                unsigned char *ydst = stg + L::BOXES * L::XB32 + bx * L::YB32;
                 if (a.gather) {
                     // sampled columns 4 lane .. 4 lane + 3: their 32 rows
                     // (128 bytes each) into tile rows 4 lane .. by one TMA
@@ -363,7 +360,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                         mma_issue<MODE>(d, desc_sw128(xl + off), desc_sw128(yh + off), idesc, 1u);
                     }
                 }
-                mma_commit(L::INPLACE ? &rfree[cs] : &cfree[cs]);
+                mma_commit(&cfree[cs]);
                 if (kc == nit - 1 || group_start(kc + 1)) mma_commit(&accf[b]);
             }
             // every MMA issued by this thread has completed once `done` flips
@@ -379,10 +376,46 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             if (s_abort) break;
             const int s = kc % L::RS;
             if (!mbar_wait(&full[s], (kc / L::RS) & 1, &s_abort, lim)) break;
-            if constexpr (L::INPLACE) {
-                unsigned char *stg = raw_stage(s);
-                auto split = [](float4 *h, float4 *lo4, int e) {
-                    const float4 v = h[e];
+            const int cs = kc % L::CS;
+            if (kc >= L::CS && !mbar_wait(&cfree[cs], ((kc / L::CS) - 1) & 1, &s_abort, lim)) break;
+            const unsigned char *stg = raw_stage(s);
+            unsigned char *cv = convb + (size_t)cs * L::CONV;
+            // row j of a tile (one X or Y column, 64 K values): FP32 chunk
+            // c of box bx at j*128 + ((c ^ (j & 7)) << 4); bf16 chunk q
+            // (rows 8q .. 8q+7) at j*128 + ((q ^ (j & 7)) << 4)
+            auto convert_row = [&](const unsigned char *raw0, int boxbytes, unsigned char *d0, unsigned char *d1, int j) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const unsigned char *rb = raw0 + (q >> 2) * boxbytes + j * 128;
+                    const int c = 2 * (q & 3);
+                    const float4 u0 = *reinterpret_cast<const float4 *>(rb + (((c) ^ (j & 7)) << 4));
+                    const float4 u1 = *reinterpret_cast<const float4 *>(rb + (((c + 1) ^ (j & 7)) << 4));
+                    const float v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                    __nv_bfloat162 h[4], l[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const __nv_bfloat16 a0 = __float2bfloat16_rn(v[2 * p]);
+                        const __nv_bfloat16 a1 = __float2bfloat16_rn(v[2 * p + 1]);
+                        h[p] = __halves2bfloat162(a0, a1);
+                        if (d1) {
+                            const float r0 = v[2 * p] - __bfloat162float(a0);
+                            const float r1 = v[2 * p + 1] - __bfloat162float(a1);
+                            l[p] = __halves2bfloat162(__float2bfloat16_rn(r0), __float2bfloat16_rn(r1));
+                        }
+                    }
+                    const int dst = j * 128 + ((q ^ (j & 7)) << 4);
+                    *reinterpret_cast<uint4 *>(d0 + dst) = *reinterpret_cast<const uint4 *>(h);
+                    if (d1) *reinterpret_cast<uint4 *>(d1 + dst) = *reinterpret_cast<const uint4 *>(l);
+                }
+            };
+            // TF32: row j's eight 16-byte chunks split into hi (low 13
+            // mantissa bits cleared) and lo = x - hi, at the same swizzled
+            // positions
+            auto split_row = [&](const unsigned char *raw0, unsigned char *d0, unsigned char *d1, int j) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int off = j * 128 + ((c ^ (j & 7)) << 4);
+                    const float4 v = *reinterpret_cast<const float4 *>(raw0 + off);
                     float4 hv, lv;
                     hv.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
                     hv.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
@@ -392,58 +425,23 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     lv.y = v.y - hv.y;
                     lv.z = v.z - hv.z;
                     lv.w = v.w - hv.w;
-                    h[e] = hv;
-                    lo4[e] = lv;
-                };
-                float4 *xh = reinterpret_cast<float4 *>(stg + L::X_HI);
-                float4 *xl = reinterpret_cast<float4 *>(stg + L::X_LO);
-                float4 *yh = reinterpret_cast<float4 *>(stg + L::Y_HI);
-                float4 *yl = reinterpret_cast<float4 *>(stg + L::Y_LO);
-                for (int e = t; e < L::XB32 / 16; e += 128) split(xh, xl, e);
-                for (int e = t; e < L::YB32 / 16; e += 128) split(yh, yl, e);
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                mbar_arrive(&ready[s]);
+                    *reinterpret_cast<float4 *>(d0 + off) = hv;
+                    *reinterpret_cast<float4 *>(d1 + off) = lv;
+                }
+            };
+            constexpr bool two = L::PRODUCTS == 3;
+            if constexpr (MODE == POD_PREC_TF32X3) {
+                split_row(stg, cv + L::X_HI, cv + L::X_LO, t);
+                if (t < NT) split_row(stg + L::XB32, cv + L::Y_HI, cv + L::Y_LO, t);
             } else {
-                const int cs = kc % L::CS;
-                if (kc >= L::CS && !mbar_wait(&cfree[cs], ((kc / L::CS) - 1) & 1, &s_abort, lim)) break;
-                const unsigned char *stg = raw_stage(s);
-                unsigned char *cv = convb + (size_t)cs * L::CONV;
-                // row j of a tile (one X or Y column, 64 K values): FP32 chunk
-                // c of box bx at j*128 + ((c ^ (j & 7)) << 4); bf16 chunk q
-                // (rows 8q .. 8q+7) at j*128 + ((q ^ (j & 7)) << 4)
-                auto convert_row = [&](const unsigned char *raw0, int boxbytes, unsigned char *d0, unsigned char *d1, int j) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const unsigned char *rb = raw0 + (q >> 2) * boxbytes + j * 128;
-                        const int c = 2 * (q & 3);
-                        const float4 u0 = *reinterpret_cast<const float4 *>(rb + (((c) ^ (j & 7)) << 4));
-                        const float4 u1 = *reinterpret_cast<const float4 *>(rb + (((c + 1) ^ (j & 7)) << 4));
-                        const float v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-                        __nv_bfloat162 h[4], l[4];
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            const __nv_bfloat16 a0 = __float2bfloat16_rn(v[2 * p]);
-                            const __nv_bfloat16 a1 = __float2bfloat16_rn(v[2 * p + 1]);
-                            h[p] = __halves2bfloat162(a0, a1);
-                            if (d1) {
-                                const float r0 = v[2 * p] - __bfloat162float(a0);
-                                const float r1 = v[2 * p + 1] - __bfloat162float(a1);
-                                l[p] = __halves2bfloat162(__float2bfloat16_rn(r0), __float2bfloat16_rn(r1));
-                            }
-                        }
-                        const int dst = j * 128 + ((q ^ (j & 7)) << 4);
-                        *reinterpret_cast<uint4 *>(d0 + dst) = *reinterpret_cast<const uint4 *>(h);
-                        if (d1) *reinterpret_cast<uint4 *>(d1 + dst) = *reinterpret_cast<const uint4 *>(l);
-                    }
-                };
-                constexpr bool two = L::PRODUCTS == 3;
                 convert_row(stg, L::XB32, cv + L::X_HI, two ? cv + L::X_LO : nullptr, t);
                 if (t < NT)
-                    convert_row(stg + L::BOXES * L::XB32, L::YB32, cv + L::Y_HI, two ? cv + L::Y_LO : nullptr, t);
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                mbar_arrive(&rfree[s]);
-                mbar_arrive(&ready[cs]);
+                    convert_row(stg + L::BOXES * L::XB32, L::YB32, cv + L::Y_HI, two ? cv + L::Y_LO : nullptr,
+                                t);
             }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(&rfree[s]);
+            mbar_arrive(&ready[cs]);
         }
     } else if (warp >= 8) {
         // ------------------------------------------------ epilogue
