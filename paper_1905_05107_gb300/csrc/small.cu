@@ -1371,6 +1371,14 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
             Vr[s * nc + p] = a0.get() + a1.get();
         }
         __syncthreads();
+        // Vr transposed into Yt (free until the Rayleigh products), so that
+        // the threads of a warp (consecutive j) read consecutive entries
+        X *VrT = Yt;
+        for (int e = tid; e < nc * rsel; e += bd) {
+            const int s2 = e / nc, p = e % nc;
+            VrT[p * rsel + s2] = Vr[e];
+        }
+        __syncthreads();
         const int rm = a.rmax;
         for (int e = tid; e < rsel * rsel; e += bd) {
             const int i = e / rsel, j = e % rsel;
@@ -1378,10 +1386,10 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
             if (i <= j) {
                 int p = 0;
                 for (; p + 1 < nc; p += 2) {
-                    a0.add(Vr[i * nc + p], Vr[j * nc + p]);
-                    a1.add(Vr[i * nc + p + 1], Vr[j * nc + p + 1]);
+                    a0.add(VrT[p * rsel + i], VrT[p * rsel + j]);
+                    a1.add(VrT[(p + 1) * rsel + i], VrT[(p + 1) * rsel + j]);
                 }
-                if (p < nc) a0.add(Vr[i * nc + p], Vr[j * nc + p]);
+                if (p < nc) a0.add(VrT[p * rsel + i], VrT[p * rsel + j]);
             }
             Gb[i * rm + j] = a0.get() + a1.get();
         }
@@ -1506,20 +1514,29 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
             Q[s * nc + p] = a0.get() + a1.get();
         }
         __syncthreads();
+        // Q transposed into Vr (no longer read): the threads of a warp take
+        // consecutive s of one column j of E (one broadcast E entry, Q
+        // entries side by side)
+        X *QT = Vr;
         for (int e = tid; e < nc * rsel; e += bd) {
-            const int s = e / nc, j = e % nc;
+            const int s2 = e / nc, p = e % nc;
+            QT[p * rsel + s2] = Q[e];
+        }
+        __syncthreads();
+        for (int e = tid; e < nc * rsel; e += bd) {
+            const int j = e / rsel, s = e % rsel;
             // column j of E: sigma_j alone for j < r, rows 0..j otherwise
             X acc = XOps<X>::zero();
             if (j < r) {
-                acc = Ex[j * nc + j] * Q[s * nc + j];
+                acc = Ex[j * nc + j] * QT[j * rsel + s];
             } else {
                 Acc<X> a0, a1;
                 int p = 0;
                 for (; p + 1 <= j; p += 2) {
-                    a0.add(Ex[j * nc + p], Q[s * nc + p]);
-                    a1.add(Ex[j * nc + p + 1], Q[s * nc + p + 1]);
+                    a0.add(Ex[j * nc + p], QT[p * rsel + s]);
+                    a1.add(Ex[j * nc + p + 1], QT[(p + 1) * rsel + s]);
                 }
-                if (p <= j) a0.add(Ex[j * nc + p], Q[s * nc + p]);
+                if (p <= j) a0.add(Ex[j * nc + p], QT[p * rsel + s]);
                 acc = a0.get() + a1.get();
             }
             Yt[s * nc + j] = acc;
@@ -1634,10 +1651,18 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     }
     // wq: Y = R2^{-1} U_E[r:, :rn], X = U_E[:r, :rn]; otherwise
     // Y = R^{-1} U_E[r:, :rn] (g x rn), X = U_E[:r, :rn] - Ptot Y (r x rn)
+    // (Q transposed into Vr, free here: the threads of a warp, consecutive
+    // q, read consecutive entries)
+    X *QTc = Vr;
+    for (int e = tid; e < nc * rsel; e += bd) {
+        const int s2 = e / nc, p = e % nc;
+        QTc[p * rsel + s2] = Q[e];
+    }
+    __syncthreads();
     for (int e = tid; e < g * rn; e += bd) {
         const int j = e / rn, q = e % rn;
         X acc = XOps<X>::zero();
-        for (int l = j; l < g; ++l) acc = acc + Rinv[j * ld + l] * Q[q * nc + r + l];
+        for (int l = j; l < g; ++l) acc = acc + Rinv[j * ld + l] * QTc[(r + l) * rsel + q];
         Yt[j * a.rmax + q] = acc;
     }
     __syncthreads();
@@ -1647,7 +1672,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(SmallArgs a) {
     }
     for (int e = tid; e < r * rn; e += bd) {
         const int l = e / rn, q = e % rn;
-        X acc = Q[q * nc + l];
+        X acc = QTc[l * rsel + q];
         if (!a.wq)
             for (int j = 0; j < g; ++j) acc = acc - Ptx[l * ld + j] * Yt[j * a.rmax + q];
         a.Xm[l * a.rmax + q] = XOps<X>::to(acc);
