@@ -568,6 +568,25 @@ __device__ void sq_matmul(const J *A, J *C, int k) {
     }
 }
 
+// Sum of v[i * stride] over i < k by warp 0 (lane partials, then a fixed
+// shuffle tree), the same value returned to every thread.  Called by the
+// whole CTA; ends with a barrier.
+template <typename J>
+__device__ J warp0_sum(const J *v, int k, int stride) {
+    __shared__ J s_sum;
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        J part = 0;
+        for (int i = tid; i < k; i += 32) part += v[(size_t)i * stride];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (tid == 0) s_sum = part;
+    }
+    __syncthreads();
+    const J r = s_sum;
+    __syncthreads();
+    return r;
+}
+
 template <typename J>
 __device__ double top_singular_value(const J *Bt, int nrow, int k, J *M, J *P, J *P2, J *x, J *y, double *red_d) {
     const int tid = threadIdx.x, bd = blockDim.x;
@@ -584,8 +603,7 @@ __device__ double top_singular_value(const J *Bt, int nrow, int k, J *M, J *P, J
         M[e] = v0 + v1;
     }
     __syncthreads();
-    J tr = 0;
-    for (int i = 0; i < k; ++i) tr += M[i * k + i];
+    const J tr = warp0_sum<J>(M, k, k + 1);
     if (!(tr > (J)0)) return 0.0;   // B = 0 (or not finite); every thread the same
     const J eps = sizeof(J) == 4 ? (J)1e-6 : (J)1e-13;
     const J itr = (J)1 / tr;
@@ -595,10 +613,8 @@ __device__ double top_singular_value(const J *Bt, int nrow, int k, J *M, J *P, J
     for (int sq = 0; sq < SQ_MAX; ++sq) {
         sq_matmul<J>(cur, nxt, k);
         __syncthreads();
-        J t2 = 0;
-        for (int i = 0; i < k; ++i) t2 += nxt[i * k + i];   // trace(cur^2) = sum of squared eigenvalues
-        if (!(t2 > (J)0)) break;                              // (every thread the same)
-        __syncthreads();
+        const J t2 = warp0_sum<J>(nxt, k, k + 1);   // trace(cur^2) = sum of squared eigenvalues
+        if (!(t2 > (J)0)) break;                    // (every thread the same)
         const J it2 = (J)1 / t2;
         for (int e = tid; e < k * k; e += bd) nxt[e] *= it2;
         __syncthreads();
@@ -607,14 +623,31 @@ __device__ double top_singular_value(const J *Bt, int nrow, int k, J *M, J *P, J
         nxt = sw;
         if (t2 > (J)1 - eps) break;                           // one eigenvalue left
     }
-    // x = the column of cur with the largest diagonal
-    int imax = 0;
-    J dmax = -1;
-    for (int i = 0; i < k; ++i)
-        if (cur[i * k + i] > dmax) {
-            dmax = cur[i * k + i];
-            imax = i;
+    // x = the column of cur with the largest diagonal (the first of equal
+    // ones), found by warp 0
+    __shared__ int s_imax;
+    if (tid < 32) {
+        J best = -1;
+        int bi = k;
+        for (int i = tid; i < k; i += 32) {
+            const J v = cur[i * k + i];
+            if (v > best) {
+                best = v;
+                bi = i;
+            }
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            const J ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (tid == 0) s_imax = bi < k ? bi : 0;
+    }
+    __syncthreads();
+    const int imax = s_imax;
     for (int i = tid; i < k; i += bd) x[i] = cur[i * k + imax];
     __syncthreads();
     for (int it = 0; it < SQ_APPLY; ++it) {
@@ -624,8 +657,16 @@ __device__ double top_singular_value(const J *Bt, int nrow, int k, J *M, J *P, J
             y[i] = v;
         }
         __syncthreads();
-        J n2 = 0;
-        for (int t = 0; t < k; ++t) n2 = fma(y[t], y[t], n2);
+        // |y|^2 (every thread the same)
+        __shared__ J s_n2;
+        if (tid < 32) {
+            J part = 0;
+            for (int t = tid; t < k; t += 32) part = fma(y[t], y[t], part);
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (tid == 0) s_n2 = part;
+        }
+        __syncthreads();
+        const J n2 = s_n2;
         const J in = n2 > (J)0 ? (J)1 / sqrt(n2) : (J)0;
         __syncthreads();
         for (int i = tid; i < k; i += bd) x[i] = y[i] * in;
@@ -639,8 +680,15 @@ __device__ double top_singular_value(const J *Bt, int nrow, int k, J *M, J *P, J
         num = fma(x[i], v, num);
     }
     num = block_sum<J>(num, red);
-    J xx = 0;
-    for (int t = 0; t < k; ++t) xx = fma(x[t], x[t], xx);
+    __shared__ J s_xx;
+    if (tid < 32) {
+        J part = 0;
+        for (int t = tid; t < k; t += 32) part = fma(x[t], x[t], part);
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (tid == 0) s_xx = part;
+    }
+    __syncthreads();
+    const J xx = s_xx;
     J lam = xx > (J)0 ? num / xx : (J)0;
     const J lower = tr / (J)k;
     lam = lam < lower ? lower : (lam > tr ? tr : lam);
