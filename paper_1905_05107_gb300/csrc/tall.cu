@@ -196,6 +196,7 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
             T a[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) a[e] = (T)0;
+#pragma unroll 2
             for (int rc = 0; rc < chunks; ++rc) {
                 T x[4][4], y[4][4];
 #pragma unroll
@@ -225,6 +226,7 @@ __device__ void gram_acc(const T *X, int na, const T *Y, int nb, int ld, int bm,
 #pragma unroll
     for (int e = 0; e < 16; ++e) a[e] = (T)0;
     if (grp < RG) {
+#pragma unroll 2
         for (int rc = grp; rc < chunks; rc += RG) {
             T x[4][4], y[4][4];
 #pragma unroll
@@ -345,6 +347,7 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
             for (int v = 0; v < 4; ++v) a1[u][v] = a2[u][v] = (T)0;
         const int k1end = tri ? min(K1, 4 * cj + 4) : K1;
         size_t soff = 4 * cj;   // S1 offset of (k, 4 cj)
+#pragma unroll 4
         for (int k = 0; k < k1end; ++k) {
             T x[4], s[4];
             lds4(A1 + (size_t)k * ld + ((rc ^ ((k >> 2) & msk)) << 2), x);
@@ -356,6 +359,7 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
 #pragma unroll
                 for (int v = 0; v < 4; ++v) a1[u][v] = fma(x[u], s[v], a1[u][v]);
         }
+#pragma unroll 4
         for (int k = 0; k < K2; ++k) {
             T x[4], s[4];
             lds4(A2 + (size_t)k * ld + ((rc ^ ((k >> 2) & msk)) << 2), x);
