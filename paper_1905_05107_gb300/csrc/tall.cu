@@ -373,6 +373,68 @@ __device__ __forceinline__ void rowspace_tiles(int bm, int N, const T *A1, int K
     }
 }
 
+// W = A S for upper triangular S with trimmed rows (tri_row_off, n4 = ls),
+// with the work balanced over the threads: output tile (rc, cj) takes the
+// k-steps 0 .. K(cj) - 1, K(cj) = min(4 cj + 4, N), cut at m(cj) =
+// min(2 cj + 2, K(cj)); thread (rc, cj) forms the first part of tile
+// (rc, cj) and the second part of tile (rc, tn - 1 - cj), about 2 tn + 2
+// steps for every thread (one tile per thread in rowspace_tiles: the thread
+// of the last column did 4 tn).  The second parts meet their first parts
+// through red (element-major, tiles x 16 T).  Needs chunks x tn <=
+// blockDim.x.  store(rc, cj, w) consumes each tile; ends with a barrier.
+template <typename T, typename Store>
+__device__ __forceinline__ void rowspace_tri_bal(int bm, int N, const T *A, const T *S, int ls, int ld, T *red,
+                                                 Store store) {
+    const int chunks = bm >> 2, tn = (N + 3) >> 2, msk = sw_mask(bm), nt = chunks * tn;
+    const int t = threadIdx.x;
+    T a[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a[u][v] = (T)0;
+    auto part = [&](int rc, int cj, int k0, int k1, T (&acc)[4][4]) {
+        size_t soff = tri_row_off(k0, ls) + 4 * cj - 4 * (k0 >> 2);
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            T x[4], sv[4];
+            lds4(A + (size_t)k * ld + ((rc ^ ((k >> 2) & msk)) << 2), x);
+            lds4(S + soff, sv);
+            soff += (size_t)(ls - 4 * (k >> 2) - ((k & 3) == 3 ? 4 : 0));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], sv[v], acc[u][v]);
+        }
+    };
+    const int rc = t % chunks, cj = t / chunks;
+    if (t < nt) {
+        const int K = min(4 * cj + 4, N), m = min(2 * cj + 2, K);
+        part(rc, cj, 0, m, a);
+        const int cj2 = tn - 1 - cj;
+        const int K2 = min(4 * cj2 + 4, N), m2 = min(2 * cj2 + 2, K2);
+        T b[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) b[u][v] = (T)0;
+        part(rc, cj2, m2, K2, b);
+        const int t2 = cj2 * chunks + rc;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) red[(size_t)(u * 4 + v) * nt + t2] = b[u][v];
+    }
+    __syncthreads();
+    if (t < nt) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a[u][v] += red[(size_t)(u * 4 + v) * nt + t];
+        store(rc, cj, a);
+    }
+    __syncthreads();
+}
+
 struct SmemPlan {
     int ld;          // slab leading dimension (= bm; the slabs are swizzled, not padded)
     int r4, c4;
@@ -688,17 +750,22 @@ __global__ void __launch_bounds__(TALL_MAX_THREADS) k_tall(TallArgs<T> a) {
                                   });
                 __syncthreads();
             }
-            rowspace_tiles<T>(bm, g, Cs, g, S3, g4, Cs, 0, S3, g4, ld, true,
-                              [&](int rc, int cj, T (&a1)[4][4], T (&)[4][4]) {
+            auto store_w = [&](int rc, int cj, T (&a1)[4][4]) {
 #pragma unroll
-                                  for (int v = 0; v < 4; ++v) {
-                                      T w[4];
+                for (int v = 0; v < 4; ++v) {
+                    T w[4];
 #pragma unroll
-                                      for (int u = 0; u < 4; ++u) w[u] = a1[u][v];
-                                      sts4(Ws + (size_t)(4 * cj + v) * ld + ((rc ^ (cj & msk)) << 2), w);
-                                  }
-                              });
-            __syncthreads();
+                    for (int u = 0; u < 4; ++u) w[u] = a1[u][v];
+                    sts4(Ws + (size_t)(4 * cj + v) * ld + ((rc ^ (cj & msk)) << 2), w);
+                }
+            };
+            if ((bm >> 2) * ((g + 3) >> 2) <= bd) {
+                rowspace_tri_bal<T>(bm, g, Cs, S3, g4, ld, red, store_w);
+            } else {
+                rowspace_tiles<T>(bm, g, Cs, g, S3, g4, Cs, 0, S3, g4, ld, true,
+                                  [&](int rc, int cj, T (&a1)[4][4], T (&)[4][4]) { store_w(rc, cj, a1); });
+                __syncthreads();
+            }
             if (a.Wout) {
                 // W itself for the UPDATE pass: Q = W R2^{-1} is then formed from
                 // the very W whose Gram gave R2 (explicit CholeskyQR2)
