@@ -19,9 +19,8 @@ namespace {
 // The one-CTA Cholesky kernels take a barrier per elimination step; with
 // O(n^2 / 4) work per step, 8 warps finish a step sooner than 32.
 constexpr int CHOL_THREADS = 256;
-// k_small_chol: up to 1024 threads (its triangular steps have up to
-// g^2 / 2 independent updates; at g = 100 1024 threads took 0.43 ms per
-// factorisation against 0.66 ms with 256, at g = 40 512 threads did best)
+// k_small_chol: up to 1024 threads for the blocked factorisation's trailing
+// updates and block products (1024 when g > 64, else 512)
 constexpr int CHOL1_MAX_THREADS = 1024;
 constexpr int CORE_THREADS = 512;
 
@@ -735,17 +734,6 @@ pod_status launch_reduce(const double *part, int nparts, int64_t stride, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// First CholeskyQR pass: Ptot = fl(P) + fl(P2), R1 = chol(Z^T Z) with pivot
-// dropping, M1 = fl(R1^{-1}) (the matrix the tall pass applies), and
-// R1p = M1^{-1} (the exact inverse of what was applied, used in E).
-// ---------------------------------------------------------------------------
-//
-// XC is the arithmetic of the Cholesky and of M1: FP32 in the plain pass of
-// FP32 data, whose Gram is only FP32-accurate anyway (M1 is rounded to FP32
-// before use, so an FP32 inverse costs no accuracy: both errors are
-// O(u kappa)); X (double-float or FP64) in the compensated rerun and for FP64
-// data.  R1p, the inverse of the applied M1, is always formed in X.
-// ---------------------------------------------------------------------------
 // Blocked forms of chol_drop and tri_inv for the first CholeskyQR kernel
 // (CB-row blocks: a few barriers per block instead of one per row).
 // ---------------------------------------------------------------------------
@@ -850,6 +838,17 @@ __device__ void tri_inv_blk(const X *R, int ldr, int n, X *M, int ldm, X *T, X *
     }
 }
 
+// ---------------------------------------------------------------------------
+// First CholeskyQR pass: Ptot = fl(P) + fl(P2), R1 = chol(Z^T Z) with pivot
+// dropping, M1 = fl(R1^{-1}) (the matrix the tall pass applies), and
+// R1p = M1^{-1} (the exact inverse of what was applied, used in E).
+// ---------------------------------------------------------------------------
+//
+// XC is the arithmetic of the Cholesky and of M1: FP32 in the plain pass of
+// FP32 data, whose Gram is only FP32-accurate anyway (M1 is rounded to FP32
+// before use, so an FP32 inverse costs no accuracy: both errors are
+// O(u kappa)); X (double-float or FP64) in the compensated rerun and for FP64
+// data.  R1p, the inverse of the applied M1, is always formed in X.
 struct Chol1Layout {
     size_t xc, x;      // one ld x ld array of XC / of X (16-byte multiples)
     size_t main;       // the larger of 3 xc and 2 x
