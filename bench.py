@@ -60,7 +60,11 @@ TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the kernel as it was when captured; the hash of
 # its sources at that time guards against reporting stale counters.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # one k_core launch (n_c = 150, the headline's core size; its traffic does
+    # not depend on m) of bench.py --only-head --m 262144 --n 2048
+    "core_svd": {"bytes": 592128, "src_sha": "6dcad455dd784916"},
+}
 KERNEL_SOURCES = {
     "core_svd": ["paper_1905_05107_gb300/csrc/small.cu", "paper_1905_05107_gb300/csrc/common.cuh",
                  "paper_1905_05107_gb300/csrc/pod_internal.h"],
