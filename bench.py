@@ -191,6 +191,42 @@ def make_head(m=0, n=0):
     return synth.make_precision_c3()      # (m, n) Fortran-ordered float32
 
 
+def shared_head(m, n, local, world):
+    """The headline matrix for N > 1 replicas: local rank 0 generates it once
+    into /dev/shm and every rank maps that file (one host copy instead of one
+    per rank, whose FP64 generation buffers alone would not fit N = 8 on one
+    host).  Returns (A as an (m, n) Fortran-ordered view, path) or (None,
+    None) when /dev/shm is missing or too small (each rank then generates its
+    own)."""
+    import shutil
+    import torch.distributed as dist
+    mm = m or 1_000_000
+    nn = n or 4000
+    path = "/dev/shm/pod_bench_head_%dx%d.f32" % (mm, nn)
+    nbytes = mm * nn * 4
+    try:
+        ok = shutil.disk_usage("/dev/shm").free > nbytes + (1 << 30) or os.path.exists(path)
+    except OSError:
+        ok = False
+    flag = [1 if ok else 0]
+    if world > 1:
+        import torch
+        t = torch.tensor(flag, dtype=torch.int32, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        flag = [int(t.item())]
+    if not flag[0]:
+        return None, None
+    if local == 0:
+        A = make_head(m, n)
+        tmp = path + ".tmp"
+        np.ascontiguousarray(A.T).tofile(tmp)   # (n, m) rows = the columns of A
+        del A
+        os.replace(tmp, path)
+    barrier(world)
+    At = np.memmap(path, dtype=np.float32, mode="r+", shape=(nn, mm))
+    return At.T, path
+
+
 def make_flow():
     from paper_1905_05107_gb300 import synth
     return synth.make_flow_316()
@@ -314,12 +350,22 @@ def kernel_model(m, es, r, g):
     }
 
 
-def time_problem(torch, pod, A_np, w, steps, warmup, dev, world, detail):
+def time_problem(torch, pod, A_np, w, steps, warmup, dev, world, detail, register=False):
     """Device-timed and end-to-end steps of one workload; with `detail`, also
-    per-kernel timings, core statistics and the refinement's A^T U."""
+    per-kernel timings, core statistics and the refinement's A^T U.  With
+    `register`, the host matrix (a shared mapping) is page-locked in place
+    instead of copied into pinned memory."""
     m, n = A_np.shape
     k = w["k"]
-    A_host = torch.from_numpy(np.ascontiguousarray(A_np.T)).pin_memory()   # (n, m) = column-major A
+    A_t = torch.from_numpy(np.ascontiguousarray(A_np.T))   # (n, m) = column-major A
+    if register:
+        cudart = torch.cuda.cudart()
+        rc = cudart.cudaHostRegister(A_t.data_ptr(), A_t.numel() * A_t.element_size(), 0)
+        if rc != cudart.cudaError.success:
+            raise RuntimeError("cudaHostRegister failed (%s)" % rc)
+        A_host = A_t
+    else:
+        A_host = A_t.pin_memory()
     A_dev_t = A_host.to(dev)
     A = A_dev_t.t()
     stream = torch.cuda.Stream(dev)
@@ -409,7 +455,10 @@ def time_problem(torch, pod, A_np, w, steps, warmup, dev, world, detail):
             per["colnorms"] = [cn[0].elapsed_time(cn[1]) / reps]
             out.update(per=per, rg=rg, sweeps=sweeps, core_cyc=core_cyc)
         ctx.close()
-    del A_dev_t, A_host
+    del A_dev_t
+    if register:
+        torch.cuda.cudart().cudaHostUnregister(A_host.data_ptr())
+    del A_host
     torch.cuda.empty_cache()
     return out
 
@@ -607,13 +656,18 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     from paper_1905_05107_gb300 import build, pod
     build.build()
-    A_np = make_head(args.m, args.n)
+    shm_path = None
+    if world > 1:
+        A_np, shm_path = shared_head(args.m, args.n, local, world)
+    if shm_path is None:
+        A_np = make_head(args.m, args.n)
     m, n = A_np.shape
     k = HEAD["k"]
     head = dict(HEAD)
     if (m, n) != (1_000_000, 4000):
         head["workload"] = "planted-%dx%d-f32" % (m, n)
-    t = time_problem(torch, pod, A_np, head, args.steps, args.warmup, dev, world, detail=True)
+    t = time_problem(torch, pod, A_np, head, args.steps, args.warmup, dev, world, detail=True,
+                     register=shm_path is not None)
     hbm, bf16, bf16_sus, peak_kind = load_peaks()
     roof = roofline_of(t, m, n, k, hbm, bf16, tc_proj=True)
     roof["peak_source"] = roof.get("peak_source", "%s: MEASURED_PEAKS.json hbm_gbs" % peak_kind)
@@ -672,6 +726,14 @@ def run_ours(args):
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:
+        if shm_path is not None:
+            del A_np
+            barrier(world)   # every rank is done with the shared matrix
+            if local == 0:
+                try:
+                    os.remove(shm_path)
+                except OSError:
+                    pass
         torch.distributed.destroy_process_group()
     return 0
 
