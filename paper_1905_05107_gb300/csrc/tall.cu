@@ -14,9 +14,12 @@
 // cp.async (16-byte copies when every column start is 16-byte aligned),
 // double-buffered so the next slab streams in while the current one is
 // used.  Every product is a 4x4 register tile fed by 128-bit shared loads:
-// the row-space products (C - U P, Z M1, U X + W Y) tile 4 rows x 4 output
-// columns, the Gram-type products (U^T C, Z^T Z) tile 4 x 4 outputs over
-// 4-row chunks.  FP32 tile sums are added into running sums after every
+// the row-space products (C - U P, Z - U P2, Z M1, U X + W Y) tile 4 rows x 4
+// output columns (the triangular Z M1 with each tile's k-range split in two
+// and balanced across the threads), the Gram-type products (U^T C, Z^T Z)
+// tile 4 x 4 outputs over 4-row chunks.  Each kind of pass has its own
+// shared-memory layout, slab height and thread count (tall_plan).  FP32 tile
+// sums are added into running sums after every
 // slab (double-float slots for FP32 data, FP64 for FP64 data).  Each CTA
 // writes its FP64 partial; in a round's PROJ, CGS and QR2 passes those are
 // summed by k_sum_parts (many CTAs, fixed order), elsewhere inside the kernel:
